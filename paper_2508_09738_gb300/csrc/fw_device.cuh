@@ -1,0 +1,506 @@
+// Device code of the Greedy Frank-Wolfe (GFW) hot path, shared by the plain
+// per-pass kernels and the persistent batched kernel.
+//
+// One GFW iteration (Alg. 3) is two passes over a problem's rows:
+//   pass A (row pass):  apply the pending update of the previous step
+//                       U <- (1-a) U + a S,  LU <- (1-a) LU + a LS   (Sec. 4, Alg. 3 step 6)
+//                       then G' = LU - (2/eps) U + D_w (U - U_hat)    (eq. gradgl_vv2g without 1/eps)
+//                       the greedy LMO choice (eq. eq:LMOpr) and the per-row pieces of
+//                       the FW gap g = -<G, D> and of ||D||^2, sum w_i ||D_i||^2, <D, LU>.
+//   pass B (CSR pass):  LS = L S for the one-hot S: (L S)_ik = [s_i = k] - sum_{j: s_j = k} W^_ij,
+//                       and the per-row <D_i, LS_i>; the last block forms
+//                       q = <D, L D> + sum w_i||D_i||^2 - (2/eps)||D||^2  (Hessian of App. C)
+//                       and the exact step a = min(1, g/q) (1 if q <= 0).
+// L U is never recomputed inside the loop: it follows the recurrence above, and a
+// separate SpMM (spmm_rows) builds it at the start and on refresh.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math_constants.h>
+#include <stdint.h>
+
+#include "fw_types.h"
+
+namespace fw {
+
+// --------------------------------------------------------------- rounding
+// Explicitly rounded operations: every instantiation and every kernel that
+// evaluates the same formula produces the same bits (no contraction choices).
+__device__ __forceinline__ float mul_(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float sub_(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub_(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float fma_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+template <typename T> __device__ __forceinline__ T inf_();
+template <> __device__ __forceinline__ float inf_<float>() { return CUDART_INF_F; }
+template <> __device__ __forceinline__ double inf_<double>() { return CUDART_INF; }
+
+// ------------------------------------------------------------ weight loads
+// Four consecutive entries of a padded CSR row (start is a multiple of 4).
+__device__ __forceinline__ void ld_w4(const float* p, float (&v)[4]) {
+    const float4 t = __ldg(reinterpret_cast<const float4*>(p));
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void ld_w4(const __nv_bfloat16* p, float (&v)[4]) {
+    // bf16 is the upper half of an fp32 pattern: widening is a shift (exact)
+    const uint2 t = __ldg(reinterpret_cast<const uint2*>(p));
+    v[0] = __uint_as_float(t.x << 16);
+    v[1] = __uint_as_float(t.x & 0xffff0000u);
+    v[2] = __uint_as_float(t.y << 16);
+    v[3] = __uint_as_float(t.y & 0xffff0000u);
+}
+__device__ __forceinline__ void ld_w4(const double* p, double (&v)[4]) {
+    const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+    const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+
+// Plain (coherent) loads for data written inside a persistent launch.
+template <typename T> __device__ __forceinline__ T ld_cg(const T* p) { return __ldcg(p); }
+
+// ------------------------------------------------------- block reductions
+// Sum NQ per-thread values over the block: FP32 (or FP64) butterfly inside each
+// warp, FP64 across the warps in a fixed order.  Thread q < NQ writes out[q].
+// Must be reached by every thread of the block.
+template <typename T, int NQ>
+__device__ __forceinline__ void block_partials(const T (&v)[NQ], double* __restrict__ out) {
+    __shared__ double red[kBlock / 32][NQ];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        T x = v[q];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) x = add_(x, __shfl_xor_sync(0xffffffffu, x, off));
+        if (lane == 0) red[warp][q] = double(x);
+    }
+    __syncthreads();
+    if (threadIdx.x < NQ) {
+        double s = 0.0;
+#pragma unroll
+        for (int w = 0; w < kBlock / 32; ++w) s = add_(s, red[w][threadIdx.x]);
+        out[threadIdx.x] = s;
+    }
+    __syncthreads();
+}
+
+// True in exactly one block: the last of `total` arrivals on *cnt.  The
+// partials the arriving blocks wrote before are visible to it afterwards.
+__device__ __forceinline__ bool last_to_arrive(uint32_t* cnt, uint32_t total) {
+    __shared__ uint32_t s_prev;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_prev = atomicAdd(cnt, 1u);
+    }
+    __syncthreads();
+    const bool last = (s_prev == total - 1);
+    if (last) __threadfence();
+    return last;
+}
+
+// Fixed-order FP64 sum of ntiles partial records of NQ doubles (L2 loads).
+// Every thread of the block must call it; out[] is valid in all threads.
+template <int NQ>
+__device__ __forceinline__ void sum_partials(const double* __restrict__ part, int ntiles,
+                                             double (&out)[NQ]) {
+    __shared__ double red[kBlock][NQ];
+    double s[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) s[q] = 0.0;
+    for (int t = threadIdx.x; t < ntiles; t += kBlock) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) s[q] = add_(s[q], __ldcg(part + (size_t)t * NQ + q));
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) red[threadIdx.x][q] = s[q];
+    __syncthreads();
+    for (int stride = kBlock / 2; stride > 0; stride >>= 1) {
+        if (threadIdx.x < stride) {
+#pragma unroll
+            for (int q = 0; q < NQ; ++q)
+                red[threadIdx.x][q] = add_(red[threadIdx.x][q], red[threadIdx.x + stride][q]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) out[q] = red[0][q];
+    __syncthreads();
+}
+
+// ------------------------------------------------------------- per-row math
+// Gradient without its constant 1/eps term, the (G)LMO choice and the per-row
+// terms of the FW gap, ||D_i||^2 and <D_i, LU_i>.
+//   binary row  <=> every stored entry is exactly 0 or 1;  supp = {k : u_k > 0}
+//   greedy:  active = !binary, s = lowest argmin of G' over supp (eq. eq:LMOpr)
+//   full:    active = every row, s = lowest argmin of G' over all classes (Alg. 2)
+//   inactive rows keep s = position of their 1.
+// moved = the row has D_i != 0 (greedy: active; full: unless u_i is already e_s).
+template <typename T, int KMAX>
+__device__ __forceinline__ void row_eval(int K, const T (&u)[KMAX], const T (&lu)[KMAX], int fidc,
+                                         T c2, T om, bool greedy, T (&G)[KMAX], int& s,
+                                         bool& moved, T& gap, T& nD, T& tLU) {
+    bool binary = true;
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k)
+        if (k < K) binary = binary && (u[k] == T(0) || u[k] == T(1));
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) {
+        if (k < K) {
+            T gk = fma_(-c2, u[k], lu[k]);
+            if (fidc >= 0) gk = fma_(om, sub_(u[k], k == fidc ? T(1) : T(0)), gk);
+            G[k] = gk;
+        }
+    }
+    const bool active = greedy ? !binary : true;
+    s = -1;
+    T gs = T(0);
+    if (active) {
+        T best = inf_<T>();
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k)
+            if (k < K && (!greedy || u[k] > T(0)) && G[k] < best) {
+                best = G[k];
+                s = k;
+            }
+        gs = best;
+        if (s < 0) {  // no finite candidate: keep the first admissible class, gap becomes NaN
+#pragma unroll
+            for (int k = KMAX - 1; k >= 0; --k)
+                if (k < K && (!greedy || u[k] > T(0))) s = k;
+            if (s < 0) s = 0;
+            gs = CUDART_NAN_F;
+        }
+    } else {
+#pragma unroll
+        for (int k = KMAX - 1; k >= 0; --k)
+            if (k < K && u[k] == T(1)) s = k;
+        if (s < 0) s = 0;
+    }
+    bool at_vertex = binary;
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k)
+        if (k == s) at_vertex = at_vertex && (u[k] == T(1));
+    moved = active && !at_vertex;
+    gap = T(0);
+    nD = T(0);
+    tLU = T(0);
+    if (moved) {
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k) {
+            if (k < K) {
+                const T d = sub_(k == s ? T(1) : T(0), u[k]);
+                gap = fma_(u[k], sub_(G[k], gs), gap);
+                nD = fma_(d, d, nD);
+                tLU = fma_(d, lu[k], tLU);
+            }
+        }
+    }
+}
+
+enum PassAMode { MODE_STEP = 0, MODE_FLUSH = 1, MODE_GRAD = 2 };
+
+template <typename T>
+struct AccA {
+    T g, nD, nW, tLU, act;
+};
+
+// Pass A over rows [r_begin, r_end) of one problem, one thread per row.
+//  MODE_STEP:  apply the pending update (if upd), evaluate, store U, LU, choice.
+//  MODE_FLUSH: apply the pending update only.
+//  MODE_GRAD:  evaluate only; G' goes to Gout (SoA), choice to chout.
+template <typename T, int KMAX, int MODE>
+__device__ __forceinline__ void passA_rows(const ProbDesc& pd, T* __restrict__ U,
+                                           T* __restrict__ LU, const T* __restrict__ LS,
+                                           uint8_t* __restrict__ choice,
+                                           const int8_t* __restrict__ fid, int r_begin, int r_end,
+                                           bool upd, T alpha, AccA<T>& acc, T* __restrict__ Gout,
+                                           uint8_t* __restrict__ chout) {
+    const int K = pd.K;
+    const int64_t np = pd.npad;
+    T* Ub = U + pd.uoff;
+    T* LUb = LU + pd.uoff;
+    const T* LSb = LS + pd.uoff;
+    const T c2 = T(2.0 * pd.inv_eps);
+    const T om = T(pd.omega0);
+    const T oma = sub_(T(1), alpha);
+    const bool greedy = pd.oracle == 0;
+    for (int r = r_begin + threadIdx.x; r < r_end; r += kBlock) {
+        const int64_t gi = pd.row0 + r;
+        T u[KMAX], lu[KMAX];
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k)
+            if (k < K) {
+                u[k] = ld_cg(Ub + k * np + r);
+                lu[k] = ld_cg(LUb + k * np + r);
+            }
+        if (MODE != MODE_GRAD && upd) {
+            const uint8_t sv = ld_cg(choice + gi);
+            const int sp = sv & 0x7f;
+#pragma unroll
+            for (int k = 0; k < KMAX; ++k)
+                if (k < K) {
+                    lu[k] = fma_(alpha, ld_cg(LSb + k * np + r), mul_(oma, lu[k]));
+                    LUb[k * np + r] = lu[k];
+                }
+            if (sv & kActiveBit) {
+#pragma unroll
+                for (int k = 0; k < KMAX; ++k)
+                    if (k < K) {
+                        u[k] = (k == sp) ? fma_(oma, u[k], alpha) : mul_(oma, u[k]);
+                        Ub[k * np + r] = u[k];
+                    }
+            }
+        }
+        if (MODE == MODE_FLUSH) continue;
+        const int f = __ldg(fid + gi);
+        T G[KMAX];
+        int s;
+        bool moved;
+        T gap, nD, tLU;
+        row_eval<T, KMAX>(K, u, lu, f, c2, om, greedy, G, s, moved, gap, nD, tLU);
+        const uint8_t cv = uint8_t(s) | (moved ? kActiveBit : uint8_t(0));
+        if (MODE == MODE_GRAD) {
+#pragma unroll
+            for (int k = 0; k < KMAX; ++k)
+                if (k < K) Gout[pd.uoff + k * np + r] = G[k];
+            chout[gi] = cv;
+        } else {
+            choice[gi] = cv;
+        }
+        acc.g = add_(acc.g, gap);
+        acc.nD = add_(acc.nD, nD);
+        if (f >= 0) acc.nW = fma_(om, nD, acc.nW);
+        acc.tLU = add_(acc.tLU, tLU);
+        acc.act = add_(acc.act, moved ? T(1) : T(0));
+    }
+}
+
+// Stage 1 of the sparse passes: for each row of a 256-row sub-tile, `L` lanes
+// walk the padded CSR row in 4-entry chunks and accumulate into per-lane bins
+// in shared memory (`sm_lane`, one KP-strided slot per thread); the lanes of a
+// row then add their slots in lane order into `sm_row[row]`.
+//   ONEHOT: bin[s_j] += w_ij            (pass B: row i of W^ S)
+//   else:   bin[k]  += w_ij * U[k][j]   (SpMM: row i of W^ U)
+template <typename T, typename WT, int KMAX, bool ONEHOT>
+__device__ __forceinline__ void csr_bins(const ProbDesc& pd, const int32_t* __restrict__ row_ptr,
+                                         const int32_t* __restrict__ col,
+                                         const WT* __restrict__ val,
+                                         const uint8_t* __restrict__ choice,
+                                         const T* __restrict__ Ub, int base, int r_end, int L,
+                                         T* __restrict__ sm_lane, T* __restrict__ sm_row) {
+    constexpr int KP = KMAX | 1;
+    const int K = pd.K;
+    const int64_t np = pd.npad;
+    const int tid = threadIdx.x;
+    const int lane = tid & (L - 1);
+    const int grp = tid / L;
+    const int R = kBlock / L;
+    T* my = sm_lane + tid * KP;
+    for (int j = 0; j < L; ++j) {
+        const int rl = grp + R * j;
+        const int r = base + rl;
+        T acc[KMAX];
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k) acc[k] = T(0);
+        if (ONEHOT) {
+#pragma unroll
+            for (int k = 0; k < KMAX; ++k)
+                if (k < K) my[k] = T(0);
+        }
+        if (r < r_end) {
+            const int64_t gi = pd.row0 + r;
+            const int e0 = __ldg(row_ptr + gi);
+            const int e1 = __ldg(row_ptr + gi + 1);
+            for (int e = e0 + 4 * lane; e < e1; e += 4 * L) {
+                const int4 c = __ldg(reinterpret_cast<const int4*>(col + e));
+                T v[4];
+                if constexpr (sizeof(WT) == 2) {
+                    float vf[4];
+                    ld_w4(val + e, vf);
+                    v[0] = vf[0]; v[1] = vf[1]; v[2] = vf[2]; v[3] = vf[3];
+                } else {
+                    ld_w4(val + e, v);
+                }
+                const int cc[4] = {c.x, c.y, c.z, c.w};
+                if (ONEHOT) {
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const int sj = ld_cg(choice + cc[t]) & 0x7f;
+                        my[sj] = add_(my[sj], v[t]);
+                    }
+                } else {
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const int64_t jl = int64_t(cc[t]) - pd.row0;
+#pragma unroll
+                        for (int k = 0; k < KMAX; ++k)
+                            if (k < K) acc[k] = fma_(v[t], ld_cg(Ub + k * np + jl), acc[k]);
+                    }
+                }
+            }
+        }
+        if (!ONEHOT) {
+#pragma unroll
+            for (int k = 0; k < KMAX; ++k)
+                if (k < K) my[k] = acc[k];
+        }
+        __syncwarp();
+        for (int k = lane; k < K; k += L) {
+            T s = T(0);
+            for (int l2 = 0; l2 < L; ++l2) s = add_(s, sm_lane[(grp * L + l2) * KP + k]);
+            sm_row[rl * KP + k] = s;
+        }
+        __syncwarp();
+    }
+}
+
+// Pass B over rows [r_begin, r_end): LS = L S (one-hot S) and sum_i <D_i, LS_i>.
+template <typename T, typename WT, int KMAX>
+__device__ __forceinline__ void passB_rows(const ProbDesc& pd, const int32_t* __restrict__ row_ptr,
+                                           const int32_t* __restrict__ col,
+                                           const WT* __restrict__ val, const T* __restrict__ diag,
+                                           const uint8_t* __restrict__ choice,
+                                           const T* __restrict__ U, T* __restrict__ LS,
+                                           int r_begin, int r_end, T& accq, T* sm_lane,
+                                           T* sm_row) {
+    constexpr int KP = KMAX | 1;
+    const int K = pd.K;
+    const int64_t np = pd.npad;
+    const T* Ub = U + pd.uoff;
+    T* LSb = LS + pd.uoff;
+    for (int base = r_begin; base < r_end; base += kBlock) {
+        csr_bins<T, WT, KMAX, true>(pd, row_ptr, col, val, choice, Ub, base, r_end, pd.lanes,
+                                    sm_lane, sm_row);
+        __syncthreads();
+        const int r = base + threadIdx.x;
+        if (r < r_end) {
+            const int64_t gi = pd.row0 + r;
+            const uint8_t sv = ld_cg(choice + gi);
+            const int si = sv & 0x7f;
+            const T dg = pd.comb ? diag[gi] : T(1);
+            T ls[KMAX];
+#pragma unroll
+            for (int k = 0; k < KMAX; ++k)
+                if (k < K) {
+                    const T b = sm_row[threadIdx.x * KP + k];
+                    ls[k] = (k == si) ? sub_(dg, b) : -b;
+                    LSb[k * np + r] = ls[k];
+                }
+            if (sv & kActiveBit) {
+                T qi = T(0);
+#pragma unroll
+                for (int k = 0; k < KMAX; ++k)
+                    if (k < K) {
+                        const T d = sub_(k == si ? T(1) : T(0), ld_cg(Ub + k * np + r));
+                        qi = fma_(d, ls[k], qi);
+                    }
+                accq = add_(accq, qi);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// OUT = L U for rows [r_begin, r_end) (SoA in and out; OUT may not alias U).
+template <typename T, typename WT, int KMAX>
+__device__ __forceinline__ void spmm_rows(const ProbDesc& pd, const int32_t* __restrict__ row_ptr,
+                                          const int32_t* __restrict__ col,
+                                          const WT* __restrict__ val, const T* __restrict__ diag,
+                                          const T* __restrict__ U, T* __restrict__ OUT,
+                                          int r_begin, int r_end, T* sm_lane, T* sm_row) {
+    constexpr int KP = KMAX | 1;
+    const int K = pd.K;
+    const int64_t np = pd.npad;
+    const T* Ub = U + pd.uoff;
+    T* Ob = OUT + pd.uoff;
+    for (int base = r_begin; base < r_end; base += kBlock) {
+        csr_bins<T, WT, KMAX, false>(pd, row_ptr, col, val, nullptr, Ub, base, r_end, pd.lanes,
+                                     sm_lane, sm_row);
+        __syncthreads();
+        const int r = base + threadIdx.x;
+        if (r < r_end) {
+            const int64_t gi = pd.row0 + r;
+            const T dg = pd.comb ? diag[gi] : T(1);
+#pragma unroll
+            for (int k = 0; k < KMAX; ++k)
+                if (k < K)
+                    Ob[k * np + r] = sub_(mul_(dg, ld_cg(Ub + k * np + r)),
+                                          sm_row[threadIdx.x * KP + k]);
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------ scalar steps
+// Run by one thread of the last block of pass A: stop test of Alg. 3 step 4.
+__device__ __forceinline__ void finish_A(const ProbDesc& pd, ProbState* st,
+                                         const double (&S)[kNumA]) {
+    st->g = S[0];
+    st->nD = S[1];
+    st->nW = S[2];
+    st->tLU = S[3];
+    st->active = int(S[4]);
+    if (!st->g0_set) {
+        st->g0 = S[0];
+        st->g0_set = 1;
+    }
+    st->has_update = 0;
+    int status = 2;  // FW_PENDING
+    int done = 0;
+    if (!isfinite(S[0]) || !isfinite(S[1]) || !isfinite(S[2]) || !isfinite(S[3])) {
+        status = -6;  // FW_ERR_NUMERIC
+        done = 1;
+    } else if (st->active == 0 || S[0] <= 0.0) {
+        status = 0;
+        done = 1;
+    } else {
+        const double thr = pd.tol_mode ? pd.gap_tol * st->g0 : pd.gap_tol;
+        if (S[0] <= thr) {
+            status = 0;
+            done = 1;
+        } else if (st->iter >= pd.max_iters) {
+            status = 1;  // FW_NOT_CONVERGED
+            done = 1;
+        }
+    }
+    st->status = status;
+    st->done = done;
+    st->cntA = 0;
+}
+
+// Run by one thread of the last block of pass B: curvature and step.
+__device__ __forceinline__ void finish_B(const ProbDesc& pd, ProbState* st,
+                                         const double (&S)[kNumB]) {
+    const double qL = S[0] - st->tLU;                       // <D, L D>
+    const double q = qL + st->nW - 2.0 * pd.inv_eps * st->nD;  // <D, H D>
+    const double g = st->g;
+    double a = 1.0;
+    if (!isfinite(q)) {
+        st->status = -6;
+        st->done = 1;
+        st->cntB = 0;
+        return;
+    }
+    if (pd.step_rule == 0) {
+        if (q > 0.0) a = fmin(1.0, g / q);
+    } else {
+        // Armijo: largest 0.5^j with E(U) - E(U + a D) = a g - a^2 q / 2 >= 1e-6 a g
+        if (q > 0.0) {
+            const double amax = 2.0 * (1.0 - 1e-6) * g / q;
+            for (int j = 0; j < 1100 && a > amax; ++j) a *= 0.5;
+        }
+    }
+    st->pLS = S[0];
+    st->q = q;
+    st->alpha = a;
+    st->E = st->E - a * g + 0.5 * a * a * q;
+    st->iter += 1;
+    st->has_update = 1;
+    st->cntB = 0;
+}
+
+}  // namespace fw

@@ -1,0 +1,6 @@
+// Kernel instantiations: iterate float, weights float.
+#include "fw_ops.cuh"
+
+namespace fw {
+Ops* make_ops_f32(int kmax) { return make_ops_t<float, float>(kmax); }
+}  // namespace fw

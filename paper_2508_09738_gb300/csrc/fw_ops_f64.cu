@@ -1,0 +1,6 @@
+// Kernel instantiations: iterate double, weights double.
+#include "fw_ops.cuh"
+
+namespace fw {
+Ops* make_ops_f64(int kmax) { return make_ops_t<double, double>(kmax); }
+}  // namespace fw

@@ -1,0 +1,278 @@
+"""GPU path vs the FP64 oracle, through the C ABI (needs a GB300)."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from gpu_helpers import TOL, agreement, lockstep, rel
+from paper_2508_09738_gb300 import binding as B
+from paper_2508_09738_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2508_09738_gb300 import build
+    build.build()
+
+
+@pytest.fixture(scope="module")
+def blobs2k():
+    return W.make_config_graph("blobs2k")
+
+
+# ------------------------------------------------------------- lockstep --
+
+@pytest.mark.parametrize("weights,tol", [("f64", 1e-9), ("f32", TOL), ("bf16", TOL)])
+def test_lockstep_blobs2k(blobs2k, weights, tol):
+    recs = lockstep(blobs2k, 60, weights=weights, tol=tol)
+    assert len(recs) == 60
+
+
+def test_lockstep_blobs2k_long_every10(blobs2k):
+    """500 iterations, checks every 10: the L U recurrence does not drift past 1e-5."""
+    recs = lockstep(blobs2k, 500, weights="f32", every=10, energy=True)
+    assert len(recs) == 50
+
+
+@pytest.mark.parametrize("L", [1, 2, 4, 8, 16, 32])
+def test_lockstep_lanes_per_row(L):
+    g = W.blobs_knn(n=1537, K=7, seed=5)       # ragged: 6 tiles of 256 + 1 row
+    lockstep(g, 12, weights="f32", lanes_per_row=L)
+
+
+@pytest.mark.parametrize("K", [2, 3, 4, 5, 8, 9, 12, 13, 16, 17, 32])
+def test_lockstep_class_counts(K):
+    g = W.blobs_knn(n=40 * K + 3, K=K, seed=100 + K, label_frac=0.1)
+    lockstep(g, 8, weights="f32")
+    lockstep(g, 4, weights="f64", tol=1e-9)
+
+
+def test_lockstep_armijo(blobs2k):
+    lockstep(blobs2k, 15, weights="f64", step="armijo", tol=1e-9)
+
+
+def test_lockstep_full_lmo(blobs2k):
+    lockstep(blobs2k, 15, weights="f64", oracle="full", tol=1e-9)
+
+
+def test_lockstep_sbm200k_full_size():
+    g = W.make_config_graph("sbm200k")
+    recs = lockstep(g, 41, weights="f32", every=20, energy=True)
+    assert len(recs) == 3
+
+
+def test_lockstep_voronoi2048_full_size():
+    g = W.make_config_graph("voronoi2048")
+    c = W.CONFIGS["voronoi2048"]
+    recs = lockstep(g, 3, weights="f32", eps=c["eps"], omega0=c["omega0"], energy=False)
+    assert len(recs) == 3
+
+
+# ---------------------------------------------------------- free running --
+
+@pytest.mark.parametrize("weights", ["f64", "f32", "bf16"])
+def test_free_running_blobs2k_agreement(blobs2k, weights):
+    c = W.CONFIGS["blobs2k"]
+    P = O.make_problem(blobs2k, c["eps"], c["omega0"], weights)
+    Uo, info = O.gfw_solve(P, max_iters=c["iters"])
+    with B.Segmenter(blobs2k, eps=c["eps"], omega0=c["omega0"], weight_dtype=weights,
+                     max_iters=c["iters"]) as s:
+        st = s.solve()
+        lab = s.labels()
+        E = s.objective()
+    assert st.status == B.FW_NOT_CONVERGED and st.iters == c["iters"] == info["iters"]
+    a = agreement(lab, O.labels_from_U(Uo))
+    assert a >= 0.999, a
+    Eo = O.energy(Uo, P)
+    assert rel(E, Eo) <= (1e-9 if weights == "f64" else 1e-4), (E, Eo)
+    if weights == "f64":
+        assert a == 1.0
+
+
+def test_free_running_sbm200k_vs_stored_oracle():
+    gold = np.load(os.path.join(HERE, "golden", "sbm200k_oracle500.npz"))
+    c = W.CONFIGS["sbm200k"]
+    g = W.make_config_graph("sbm200k")
+    assert int(gold["nnz"]) == g.nnz
+    with B.Segmenter(g, eps=c["eps"], omega0=c["omega0"], weight_dtype="f32",
+                     max_iters=c["iters"]) as s:
+        st = s.solve()
+        lab = s.labels()
+        E = s.objective()
+    assert st.iters == int(gold["iters"])
+    a = agreement(lab, gold["labels"])
+    assert a >= 0.999, a
+    assert rel(E, float(gold["energy"])) <= 1e-4
+
+
+# ------------------------------------------------------------- one shot --
+
+def test_voronoi2048_one_shot_closed_form():
+    """eps < 1: alpha_0 = 1 and the result is the row argmin of L_s U_hat on the
+    unlabelled pixels (Alg. 4 / Cor. nonconvb2)."""
+    c = W.CONFIGS["voronoi2048_oneshot"]
+    g = W.make_config_graph("voronoi2048_oneshot")
+    with B.Segmenter(g, eps=c["eps"], omega0=c["omega0"], weight_dtype="f32",
+                     max_iters=c["iters"]) as s:
+        st = s.solve()
+        lab = s.labels()
+        U = s.U()
+    assert st.status == B.FW_OK and st.iters == 1 and st.alpha == 1.0
+    assert np.all((U == 0) | (U == 1))
+    P = O.make_problem(g, c["eps"], c["omega0"], "f32")
+    LU0 = P.L @ P.Uhat
+    target = np.argmin(LU0, axis=1)
+    unl = g.labels < 0
+    # rows whose two smallest entries are closer than FP32 resolution may flip
+    part = np.sort(LU0, axis=1)
+    safe = (part[:, 1] - part[:, 0]) > 1e-5 * np.maximum(1.0, np.abs(part[:, 0]))
+    assert np.array_equal(lab[unl & safe], target[unl & safe])
+    assert agreement(lab[unl], target[unl]) >= 0.999
+    assert np.array_equal(lab[~unl], g.labels[~unl])
+
+
+# ---------------------------------------------------------- edge cases --
+
+def test_hand_example_path3():
+    fx = json.load(open(os.path.join(HERE, "golden", "path3_tie.json")))
+    g = W.Graph(fx["n"], np.array(fx["row_ptr"], np.int32), np.array(fx["col"], np.int32),
+                np.array(fx["w"]), fx["K"], np.array(fx["labels"], np.int32),
+                np.zeros(fx["n"], np.int32))
+    for wd in ("f64", "f32"):
+        with B.Segmenter(g, eps=fx["eps"], omega0=fx["omega0"], weight_dtype=wd) as s:
+            Gp, ch, act = s.grad()
+            want = np.array(fx["grad0"]) - 1.0 / fx["eps"]
+            assert np.max(np.abs(Gp - want)) < (1e-15 if wd == "f64" else 1e-6)
+            assert ch.tolist() == fx["s0"] and act.tolist() == fx["active0"]
+            assert abs(s.objective() - fx["E0"]) < (1e-15 if wd == "f64" else 1e-6)
+            st = s.solve()
+            assert st.status == B.FW_OK and st.iters == 0 and st.gap == 0.0
+
+
+def test_all_labelled_is_stationary():
+    g = W.blobs_knn(n=300, K=3, seed=9)
+    g.labels = g.truth.copy()
+    with B.Segmenter(g) as s:
+        st = s.solve()
+        assert st.status == B.FW_OK and st.iters == 0 and st.active_rows == 0
+        assert np.array_equal(s.labels(), g.truth)
+
+
+def test_max_iters_zero_and_no_labels():
+    g = W.blobs_knn(n=300, K=3, seed=9)
+    with B.Segmenter(g, max_iters=0) as s:
+        st = s.solve()
+        assert st.status == B.FW_NOT_CONVERGED and st.iters == 0
+    g.labels[:] = -1
+    lockstep(g, 5, weights="f32")
+
+
+def test_invalid_graphs_rejected():
+    base = W.blobs_knn(n=64, K=3, seed=2)
+
+    def mk(rp, col, w):
+        return B.fw_seg_create(base.n, rp, col, w, base.K, base.labels)
+
+    rp, col, w = base.row_ptr.copy(), base.col.copy(), base.w.copy()
+    w2 = w.copy(); w2[0] *= 1.5
+    cases = []
+    cases.append((rp, col, w2, B.FW_ERR_GRAPH))                      # asymmetric
+    c3 = col.copy(); c3[0] = base.n + 5
+    cases.append((rp, c3, w, B.FW_ERR_GRAPH))                        # out of range
+    w4 = w.copy(); w4[3] = -1.0
+    cases.append((rp, col, w4, B.FW_ERR_GRAPH))                      # negative
+    w5 = w.copy(); w5[7] = np.nan
+    cases.append((rp, col, w5, B.FW_ERR_GRAPH))                      # NaN
+    c6 = col.copy(); c6[rp[1]] = 1                                   # self loop in row 1
+    cases.append((rp, c6, w, B.FW_ERR_GRAPH))
+    for rp_, col_, w_, want in cases:
+        with pytest.raises(B.FwError) as e:
+            mk(rp_, col_, w_)
+        assert e.value.status == want
+    # isolated node: an empty row 0 (and its edges removed from the others)
+    keep = np.ones(base.nnz, bool)
+    rows = np.repeat(np.arange(base.n), np.diff(base.row_ptr))
+    keep &= (rows != 0) & (base.col != 0)
+    counts = np.bincount(rows[keep], minlength=base.n)
+    rpi = np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)
+    with pytest.raises(B.FwError) as e:
+        mk(rpi, base.col[keep], base.w[keep])
+    assert e.value.status == B.FW_ERR_ISOLATED
+
+
+def test_deterministic_bitwise(blobs2k):
+    outs = []
+    for _ in range(2):
+        with B.Segmenter(blobs2k, max_iters=200, weight_dtype="f32") as s:
+            s.solve()
+            outs.append(s.U())
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_graph_launch_equals_stepwise(blobs2k):
+    with B.Segmenter(blobs2k, max_iters=70, weight_dtype="f32", iters_per_launch=16) as s:
+        s.solve()
+        U1 = s.U()
+    with B.Segmenter(blobs2k, max_iters=70, weight_dtype="f32") as s:
+        for _ in range(80):
+            if s.step(1).status != B.FW_PENDING:
+                break
+        U2 = s.U()
+    assert np.array_equal(U1, U2)
+
+
+def test_set_U_roundtrip_and_lockstep(blobs2k):
+    rng = np.random.default_rng(3)
+    U = rng.dirichlet(np.ones(blobs2k.K), size=blobs2k.n)
+    with B.Segmenter(blobs2k, weight_dtype="f64") as s:
+        s.set_U(U)
+        assert np.array_equal(s.U(), U)
+        P = O.make_problem(blobs2k, 50.0, 1000.0, "f64")
+        Gp, ch, act = s.grad()
+        assert np.max(np.abs(Gp - (O.gradient(U, P) - P.inv_eps))) < 1e-12
+        assert rel(s.objective(), O.energy(U, P)) < 1e-12
+
+
+def test_refresh_keeps_gradient_accurate():
+    g = W.make_config_graph("blobs2k")
+    P = O.make_problem(g, 50.0, 1000.0, "f32")
+    with B.Segmenter(g, weight_dtype="f32", max_iters=300, refresh_every=50) as s:
+        s.solve()
+        U = s.U()
+        Gp, _, _ = s.grad()
+    Go = O.gradient(U, P) - P.inv_eps
+    assert np.max(np.abs(Gp - Go)) / np.max(np.abs(Go)) < TOL
+
+
+def test_linear_solve_special_case_on_gpu():
+    """L = D - W, no penalty, full LMO: FW converges to (L + D_w)^-1 D_w U_hat."""
+    rng = np.random.default_rng(77)
+    n, K = 60, 3
+    perm = rng.permutation(n)
+    I = list(perm[:-1]); J = list(perm[1:])
+    for a in range(n):
+        for b in range(a + 1, n):
+            if rng.random() < 0.08:
+                I.append(a); J.append(b)
+    rp, col, w = W.from_edges(n, np.array(I), np.array(J), rng.uniform(0.1, 1.0, len(I)))
+    labels = np.full(n, -1, np.int32)
+    pick = rng.choice(n, 6, replace=False)
+    labels[pick] = rng.integers(0, K, 6)
+    g = W.Graph(n, rp, col, w, K, labels, np.zeros(n, np.int32))
+    P = O.make_problem(g, math.inf, 5.0, kind="comb")
+    A = P.L.toarray()
+    M = A + np.diag(P.omega)
+    Ustar = np.linalg.solve(M, np.diag(P.omega) @ P.Uhat)
+    with B.Segmenter(g, eps=math.inf, omega0=5.0, weight_dtype="f64", laplacian="comb",
+                     oracle="full", max_iters=3000) as s:
+        s.solve()
+        U = s.U()
+    Uo, _ = O.gfw_solve(P, max_iters=3000, oracle="full")
+    assert np.max(np.abs(U - Uo)) < 1e-9
+    assert np.max(np.abs(U - Ustar)) < 0.02

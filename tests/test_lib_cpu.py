@@ -1,0 +1,106 @@
+"""CPU-side checks of the CUDA library and its binding (no GPU needed)."""
+import ast
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+PKG = os.path.join(ROOT, "paper_2508_09738_gb300")
+
+
+def declared_functions():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"^[A-Za-z_][\w \*]*?\b(fw_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2508_09738_gb300 import build as B
+    return B.build()
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True,
+                         check=True).stdout
+    exported = set(re.findall(r" T (fw_\w+)", out))
+    decl = declared_functions()
+    assert decl, "no declarations found"
+    missing = [d for d in decl if d not in exported]
+    assert not missing, missing
+
+
+def test_binding_covers_header(libpath):
+    from paper_2508_09738_gb300 import binding as Bd
+    Bd.lib()  # loads without a GPU
+    for name in declared_functions():
+        assert hasattr(Bd.lib(), name)
+        assert hasattr(Bd, name) or name in Bd._SIGS, name
+
+
+def test_defaults_and_footprint(libpath):
+    from paper_2508_09738_gb300 import binding as Bd
+    o = Bd.fw_seg_default_opts()
+    assert (o.eps, o.omega0, o.max_iters, o.weight_dtype, o.oracle, o.step_rule) == \
+        (50.0, 1000.0, 500, 0, 0, 0)
+    f32 = Bd.fw_seg_footprint(200_000, 4_400_000, 10, "f32")
+    bf16 = Bd.fw_seg_footprint(200_000, 4_400_000, 10, "bf16")
+    assert bf16 < f32
+    # at least CSR + the three iterate arrays
+    assert f32 > 4_400_000 * 8 + 3 * 4 * 200_000 * 10
+
+
+def test_create_without_gpu_reports_cuda_error(libpath):
+    """No silent CPU fallback: without a device the call fails with a status."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2508_09738_gb300 import binding as Bd
+    from paper_2508_09738_gb300 import workloads as W
+    g = W.blobs_knn(n=50, K=3, seed=1)
+    with pytest.raises(Bd.FwError) as e:
+        Bd.fw_seg_create(g.n, g.row_ptr, g.col, g.w, g.K, g.labels)
+    assert e.value.status == Bd.FW_ERR_CUDA
+
+
+def test_invalid_arguments_rejected_before_device_use(libpath):
+    from paper_2508_09738_gb300 import binding as Bd
+    import numpy as np
+    rp = np.array([0, 1, 2], np.int32)
+    col = np.array([1, 0], np.int32)
+    w = np.ones(2)
+    with pytest.raises(Bd.FwError) as e:
+        Bd.fw_seg_create(2, rp, col, w, 1, np.array([-1, -1], np.int32))
+    assert e.value.status == Bd.FW_ERR_UNSUPPORTED
+    with pytest.raises(Bd.FwError) as e:
+        Bd.fw_seg_create(2, rp, col, w, 3, np.array([5, -1], np.int32))
+    assert e.value.status == Bd.FW_ERR_INVALID_ARG
+    with pytest.raises(Bd.FwError) as e:
+        Bd.fw_seg_create(2, np.array([0, 2, 1], np.int32), col, w, 3, np.array([0, -1], np.int32))
+    assert e.value.status == Bd.FW_ERR_GRAPH
+    with pytest.raises(Bd.FwError) as e:
+        Bd.fw_seg_create(2, rp, col, w, 3, np.array([0, -1], np.int32),
+                         Bd.fw_seg_default_opts(eps=-1.0))
+    assert e.value.status == Bd.FW_ERR_INVALID_ARG
+
+
+def test_product_code_never_imports_oracle():
+    """The CUDA path and its binding share no code with the oracle."""
+    for dirpath, _, files in os.walk(PKG):
+        for f in files:
+            p = os.path.join(dirpath, f)
+            if f.endswith(".py"):
+                tree = ast.parse(open(p).read())
+                for node in ast.walk(tree):
+                    if isinstance(node, ast.Import):
+                        assert all(not a.name.startswith("oracle") for a in node.names), p
+                    if isinstance(node, ast.ImportFrom):
+                        assert not (node.module or "").startswith("oracle"), p
+            if f.endswith((".cu", ".cuh", ".h", ".cpp")):
+                assert "oracle/" not in open(p).read(), p
