@@ -171,6 +171,137 @@ fw_status fw_seg_get_stats(fw_seg *h, fw_seg_stats *stats);
 
 void fw_seg_destroy(fw_seg *h);
 
+/* ------------------------------------------------------------------------
+ * Batched solves: many independent problems in one persistent launch.
+ *
+ * All problems of a batch live in one contiguous device pool (each at its own
+ * offsets) and iterate together in a cooperative persistent kernel: phase A
+ * (pass A row tiles of every live problem), grid barrier, phase B, grid
+ * barrier, per iteration.  Each problem keeps its own tile partition and
+ * reduction order, so its iterates are bitwise the same as when it is solved
+ * alone (by fw_seg_* or in any other batch).  Each problem stops on its own
+ * stop rule; later launches skip it.  Waits at the grid barrier are bounded
+ * by spin_budget_ms: a wait that runs out ends the launch with FW_ERR_TIMEOUT
+ * instead of hanging.
+ * ---------------------------------------------------------------------- */
+
+/* A graph on the host (see fw_seg_create for the CSR conventions). */
+typedef struct fw_graph {
+    int64_t n;
+    const int32_t *row_ptr_host;
+    const int32_t *col_host;
+    const double *w_host;
+    int32_t K;
+    int32_t reserved;
+    const int32_t *labels_host;
+} fw_graph;
+
+enum { FW_SCHED_AUTO = 0, FW_SCHED_STATIC = 1, FW_SCHED_DYNAMIC = 2 };
+
+typedef struct fw_batch_opts {
+    int32_t weight_dtype;      /* FW_WEIGHTS_*, shared by every problem */
+    int32_t blocks_per_sm;     /* 0: autotune (cached) */
+    int32_t schedule;          /* FW_SCHED_*: static grid stride or atomic work counter */
+    int32_t iters_per_launch;  /* 0: every iteration in one launch */
+    int32_t use_graph;         /* 1: capture the launch in a CUDA graph and replay it */
+    int32_t spin_budget_ms;    /* bound on one grid-barrier wait */
+    int32_t test_barrier_extra;/* test hook, keep 0: the barrier also waits for this many
+                                  blocks that never arrive, so every wait runs out */
+    int32_t reserved;
+    const char *tune_cache;    /* autotune cache file; NULL: $FW_TUNE_CACHE or none */
+    void *cuda_stream;         /* cudaStream_t; NULL: the batch makes one */
+} fw_batch_opts;
+
+typedef struct fw_batch_info {
+    int32_t grid;              /* blocks of the persistent launch */
+    int32_t blocks_per_sm;
+    int32_t schedule;          /* FW_SCHED_STATIC or FW_SCHED_DYNAMIC */
+    int32_t graph_captured;    /* 1 if the launch runs from a CUDA graph */
+    int32_t tuned;             /* 0 set by the caller, 1 measured now, 2 from the cache */
+    int32_t kmax;              /* class bound of the compiled kernel */
+    double tune_ms;            /* time spent autotuning */
+    size_t pool_bytes;         /* device bytes of the problem pool */
+} fw_batch_info;
+
+typedef struct fw_batch fw_batch;
+
+fw_status fw_batch_default_opts(fw_batch_opts *opts);
+
+/* Create a batch of P problems.  graphs[P] are host graphs, opts[P] their
+ * solver options (eps, omega0, stop rule, ... may differ per problem; the
+ * weight dtype comes from bopts).  bopts may be NULL (defaults). */
+fw_status fw_batch_create(fw_batch **out, int32_t P, const fw_graph *graphs,
+                          const fw_seg_opts *opts, const fw_batch_opts *bopts);
+
+/* Iterate every problem to its stop rule.  stats[P] may be NULL. */
+fw_status fw_batch_solve(fw_batch *b, fw_seg_stats *stats);
+
+/* Restart every problem at U_0 on the device. */
+fw_status fw_batch_reset(fw_batch *b);
+
+fw_status fw_batch_labels(fw_batch *b, int32_t p, int32_t *labels_host);
+fw_status fw_batch_get_U(fw_batch *b, int32_t p, double *U_host);
+fw_status fw_batch_get_info(fw_batch *b, fw_batch_info *info);
+void fw_batch_destroy(fw_batch *b);
+
+/* ------------------------------------------------------------------------
+ * Serving: continuous batching of segmentation requests.
+ *
+ * A worker thread owns a device pool of hbm_budget_bytes.  Submitted requests
+ * wait in a FIFO queue; a request is admitted when a slot is free and its
+ * device footprint fits in the free pool, uploaded and assembled on a side
+ * stream while the current epoch runs, and joins the next epoch.  An epoch is
+ * one persistent launch of iters_per_epoch iterations over every resident
+ * request.  Requests that meet their stop rule are harvested (labels copied to
+ * the host) and their memory is reused.  Results are bitwise the same as when
+ * the request is solved alone.
+ * ---------------------------------------------------------------------- */
+
+typedef struct fw_srv_opts {
+    size_t hbm_budget_bytes;   /* device pool for resident requests */
+    int32_t max_slots;         /* requests resident at once */
+    int32_t max_K;             /* largest K accepted (kernel class bound) */
+    int32_t weight_dtype;      /* FW_WEIGHTS_*, shared by all requests */
+    int32_t iters_per_epoch;
+    int32_t blocks_per_sm;     /* 0: largest co-resident grid */
+    int32_t schedule;          /* FW_SCHED_* (AUTO: dynamic) */
+    int32_t spin_budget_ms;
+    int32_t reserved;
+    void *cuda_stream;         /* stream of the epochs; NULL: the server makes one */
+} fw_srv_opts;
+
+typedef struct fw_srv_info {
+    uint64_t submitted, admitted, rejected, completed, failed, epochs;
+    int32_t resident;          /* requests on the device now */
+    int32_t queued;            /* requests waiting for admission */
+    size_t pool_bytes, pool_used;
+} fw_srv_info;
+
+typedef struct fw_srv fw_srv;
+
+fw_status fw_srv_default_opts(fw_srv_opts *opts);
+fw_status fw_srv_create(fw_srv **out, const fw_srv_opts *opts);
+
+/* Queue a request; the graph is copied, so the caller's arrays may be reused
+ * at once.  FW_PENDING and a ticket on success; FW_ERR_NO_MEMORY when the
+ * request can never fit the pool (rejected); FW_ERR_UNSUPPORTED for K above
+ * max_K; other errors as fw_seg_create. */
+fw_status fw_srv_submit(fw_srv *s, const fw_graph *g, const fw_seg_opts *opts, uint64_t *ticket);
+
+/* FW_PENDING while queued or running; the request's final status once done,
+ * with labels_host[n] (nullable) and stats (nullable) filled.  A finished
+ * ticket is forgotten after it has been returned once. */
+fw_status fw_srv_poll(fw_srv *s, uint64_t ticket, int32_t *labels_host, fw_seg_stats *stats);
+
+/* As fw_srv_poll, blocking up to timeout_ms (negative: no limit). */
+fw_status fw_srv_wait(fw_srv *s, uint64_t ticket, int32_t timeout_ms, int32_t *labels_host,
+                      fw_seg_stats *stats);
+
+fw_status fw_srv_get_info(fw_srv *s, fw_srv_info *info);
+
+/* Stop the worker (requests still queued or resident are dropped) and free. */
+void fw_srv_destroy(fw_srv *s);
+
 /* Message of the last error on the calling thread ("" if none). */
 const char *fw_seg_last_error(void);
 

@@ -50,6 +50,48 @@ class fw_seg_stats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class fw_graph(ctypes.Structure):
+    _fields_ = [("n", c_int64), ("row_ptr_host", c_void_p), ("col_host", c_void_p),
+                ("w_host", c_void_p), ("K", c_int32), ("reserved", c_int32),
+                ("labels_host", c_void_p)]
+
+
+class fw_batch_opts(ctypes.Structure):
+    _fields_ = [("weight_dtype", c_int32), ("blocks_per_sm", c_int32), ("schedule", c_int32),
+                ("iters_per_launch", c_int32), ("use_graph", c_int32),
+                ("spin_budget_ms", c_int32), ("test_barrier_extra", c_int32),
+                ("reserved", c_int32), ("tune_cache", ctypes.c_char_p), ("cuda_stream", c_void_p)]
+
+
+class fw_batch_info(ctypes.Structure):
+    _fields_ = [("grid", c_int32), ("blocks_per_sm", c_int32), ("schedule", c_int32),
+                ("graph_captured", c_int32), ("tuned", c_int32), ("kmax", c_int32),
+                ("tune_ms", c_double), ("pool_bytes", c_size_t)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class fw_srv_opts(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", c_size_t), ("max_slots", c_int32), ("max_K", c_int32),
+                ("weight_dtype", c_int32), ("iters_per_epoch", c_int32),
+                ("blocks_per_sm", c_int32), ("schedule", c_int32), ("spin_budget_ms", c_int32),
+                ("reserved", c_int32), ("cuda_stream", c_void_p)]
+
+
+class fw_srv_info(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("admitted", ctypes.c_uint64),
+                ("rejected", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("failed", ctypes.c_uint64), ("epochs", ctypes.c_uint64),
+                ("resident", c_int32), ("queued", c_int32), ("pool_bytes", c_size_t),
+                ("pool_used", c_size_t)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+SCHED = {"auto": 0, "static": 1, "dynamic": 2}
+
 _lib = None
 
 _SIGS = {
@@ -70,6 +112,24 @@ _SIGS = {
     "fw_seg_reset": (c_int32, [c_void_p]),
     "fw_seg_profile": (c_int32, [c_void_p, c_int32, POINTER(c_double), POINTER(c_double)]),
     "fw_seg_destroy": (None, [c_void_p]),
+    "fw_batch_default_opts": (c_int32, [POINTER(fw_batch_opts)]),
+    "fw_batch_create": (c_int32, [POINTER(c_void_p), c_int32, POINTER(fw_graph),
+                                  POINTER(fw_seg_opts), POINTER(fw_batch_opts)]),
+    "fw_batch_solve": (c_int32, [c_void_p, POINTER(fw_seg_stats)]),
+    "fw_batch_reset": (c_int32, [c_void_p]),
+    "fw_batch_labels": (c_int32, [c_void_p, c_int32, c_void_p]),
+    "fw_batch_get_U": (c_int32, [c_void_p, c_int32, c_void_p]),
+    "fw_batch_get_info": (c_int32, [c_void_p, POINTER(fw_batch_info)]),
+    "fw_batch_destroy": (None, [c_void_p]),
+    "fw_srv_default_opts": (c_int32, [POINTER(fw_srv_opts)]),
+    "fw_srv_create": (c_int32, [POINTER(c_void_p), POINTER(fw_srv_opts)]),
+    "fw_srv_submit": (c_int32, [c_void_p, POINTER(fw_graph), POINTER(fw_seg_opts),
+                                POINTER(ctypes.c_uint64)]),
+    "fw_srv_poll": (c_int32, [c_void_p, ctypes.c_uint64, c_void_p, POINTER(fw_seg_stats)]),
+    "fw_srv_wait": (c_int32, [c_void_p, ctypes.c_uint64, c_int32, c_void_p,
+                              POINTER(fw_seg_stats)]),
+    "fw_srv_get_info": (c_int32, [c_void_p, POINTER(fw_srv_info)]),
+    "fw_srv_destroy": (None, [c_void_p]),
 }
 
 # symbols every build of the library must export (checked by the CPU tests)
@@ -279,3 +339,215 @@ class Segmenter:
 
     def profile(self, iters):
         return fw_seg_profile(self.h, iters)
+
+
+# ------------------------------------------------------------------ batches --
+
+def _graph_struct(g, keep: list) -> fw_graph:
+    rp = np.ascontiguousarray(g.row_ptr, dtype=np.int32)
+    cl = np.ascontiguousarray(g.col, dtype=np.int32)
+    ww = np.ascontiguousarray(g.w, dtype=np.float64)
+    lb = np.ascontiguousarray(g.labels, dtype=np.int32)
+    keep += [rp, cl, ww, lb]
+    return fw_graph(int(g.n), rp.ctypes.data, cl.ctypes.data, ww.ctypes.data, int(g.K), 0,
+                    lb.ctypes.data)
+
+
+def fw_batch_default_opts(**kw) -> fw_batch_opts:
+    o = fw_batch_opts()
+    _check(lib().fw_batch_default_opts(ctypes.byref(o)))
+    for k, v in kw.items():
+        if k == "weight_dtype" and isinstance(v, str):
+            v = WEIGHTS[v]
+        if k == "schedule" and isinstance(v, str):
+            v = SCHED[v]
+        if k == "tune_cache" and isinstance(v, str):
+            v = v.encode()
+        if k == "cuda_stream" and v is not None and not isinstance(v, int):
+            v = int(getattr(v, "cuda_stream", v))
+        setattr(o, k, v)
+    return o
+
+
+class BatchHandle:
+    def __init__(self, ptr, graphs):
+        self.ptr = ptr
+        self.sizes = [(int(g.n), int(g.K)) for g in graphs]
+
+
+def fw_batch_create(graphs, opts, bopts: fw_batch_opts = None) -> BatchHandle:
+    """graphs: sequence of Graph-like objects; opts: one fw_seg_opts or one per graph."""
+    P = len(graphs)
+    keep = []
+    garr = (fw_graph * P)(*[_graph_struct(g, keep) for g in graphs])
+    if isinstance(opts, fw_seg_opts):
+        opts = [opts] * P
+    oarr = (fw_seg_opts * P)(*opts)
+    out = c_void_p()
+    _check(lib().fw_batch_create(ctypes.byref(out), P, garr, oarr,
+                                 ctypes.byref(bopts) if bopts is not None else None))
+    return BatchHandle(out, graphs)
+
+
+def fw_batch_solve(b: BatchHandle):
+    P = len(b.sizes)
+    st = (fw_seg_stats * P)()
+    _check(lib().fw_batch_solve(b.ptr, st))
+    return list(st)
+
+
+def fw_batch_reset(b: BatchHandle) -> None:
+    _check(lib().fw_batch_reset(b.ptr))
+
+
+def fw_batch_labels(b: BatchHandle, p: int) -> np.ndarray:
+    out = np.empty(b.sizes[p][0], dtype=np.int32)
+    _check(lib().fw_batch_labels(b.ptr, int(p), _ptr(out)))
+    return out
+
+
+def fw_batch_get_U(b: BatchHandle, p: int) -> np.ndarray:
+    n, K = b.sizes[p]
+    U = np.empty((n, K), dtype=np.float64)
+    _check(lib().fw_batch_get_U(b.ptr, int(p), _ptr(U)))
+    return U
+
+
+def fw_batch_get_info(b: BatchHandle) -> fw_batch_info:
+    i = fw_batch_info()
+    _check(lib().fw_batch_get_info(b.ptr, ctypes.byref(i)))
+    return i
+
+
+def fw_batch_destroy(b: BatchHandle) -> None:
+    if b and b.ptr:
+        lib().fw_batch_destroy(b.ptr)
+        b.ptr = c_void_p()
+
+
+class Batch:
+    """Context-managed batch of independent problems (one persistent launch)."""
+
+    def __init__(self, graphs, opts=None, **bopts):
+        if opts is None:
+            opts = fw_seg_default_opts()
+        elif isinstance(opts, dict):
+            opts = fw_seg_default_opts(**opts)
+        elif isinstance(opts, (list, tuple)):
+            opts = [fw_seg_default_opts(**o) if isinstance(o, dict) else o for o in opts]
+        self.b = fw_batch_create(graphs, opts, fw_batch_default_opts(**bopts))
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def close(self):
+        fw_batch_destroy(self.b)
+
+    def solve(self):
+        return fw_batch_solve(self.b)
+
+    def reset(self):
+        fw_batch_reset(self.b)
+
+    def labels(self, p):
+        return fw_batch_labels(self.b, p)
+
+    def U(self, p):
+        return fw_batch_get_U(self.b, p)
+
+    def info(self):
+        return fw_batch_get_info(self.b)
+
+
+# ------------------------------------------------------------------ serving --
+
+def fw_srv_default_opts(**kw) -> fw_srv_opts:
+    o = fw_srv_opts()
+    _check(lib().fw_srv_default_opts(ctypes.byref(o)))
+    for k, v in kw.items():
+        if k == "weight_dtype" and isinstance(v, str):
+            v = WEIGHTS[v]
+        if k == "schedule" and isinstance(v, str):
+            v = SCHED[v]
+        if k == "cuda_stream" and v is not None and not isinstance(v, int):
+            v = int(getattr(v, "cuda_stream", v))
+        setattr(o, k, v)
+    return o
+
+
+def fw_srv_create(opts: fw_srv_opts = None):
+    out = c_void_p()
+    _check(lib().fw_srv_create(ctypes.byref(out), ctypes.byref(opts) if opts is not None else None))
+    return out
+
+
+def fw_srv_submit(s, g, opts: fw_seg_opts = None) -> int:
+    keep = []
+    gs = _graph_struct(g, keep)
+    t = ctypes.c_uint64()
+    _check(lib().fw_srv_submit(s, ctypes.byref(gs), ctypes.byref(opts) if opts is not None else None,
+                               ctypes.byref(t)))
+    return int(t.value)
+
+
+def fw_srv_poll(s, ticket: int, n: int):
+    """(status, labels or None, stats); status FW_PENDING while not finished."""
+    lab = np.empty(n, dtype=np.int32)
+    st = fw_seg_stats()
+    rc = lib().fw_srv_poll(s, ctypes.c_uint64(ticket), _ptr(lab), ctypes.byref(st))
+    if rc == FW_PENDING:
+        return rc, None, None
+    return rc, lab, st
+
+
+def fw_srv_wait(s, ticket: int, n: int, timeout_ms: int = -1):
+    lab = np.empty(n, dtype=np.int32)
+    st = fw_seg_stats()
+    rc = lib().fw_srv_wait(s, ctypes.c_uint64(ticket), int(timeout_ms), _ptr(lab), ctypes.byref(st))
+    if rc == FW_PENDING:
+        return rc, None, None
+    return rc, lab, st
+
+
+def fw_srv_get_info(s) -> fw_srv_info:
+    i = fw_srv_info()
+    _check(lib().fw_srv_get_info(s, ctypes.byref(i)))
+    return i
+
+
+def fw_srv_destroy(s) -> None:
+    if s:
+        lib().fw_srv_destroy(s)
+
+
+class Server:
+    """Context-managed continuous-batching server."""
+
+    def __init__(self, **opts):
+        self.s = fw_srv_create(fw_srv_default_opts(**opts))
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def close(self):
+        if self.s:
+            fw_srv_destroy(self.s)
+            self.s = None
+
+    def submit(self, g, **opts) -> int:
+        return fw_srv_submit(self.s, g, fw_seg_default_opts(**opts))
+
+    def poll(self, ticket, n):
+        return fw_srv_poll(self.s, ticket, n)
+
+    def wait(self, ticket, n, timeout_ms=-1):
+        return fw_srv_wait(self.s, ticket, n, timeout_ms)
+
+    def info(self):
+        return fw_srv_get_info(self.s)

@@ -1,0 +1,169 @@
+// Persistent batched kernel: many independent problems iterate together in
+// one cooperative launch.  Each launch runs `iters` GFW iterations; one
+// iteration is phase A (row tiles of every live problem), a grid barrier,
+// phase B (same tiles), a grid barrier.  A block takes (problem, tile) work
+// items in a static grid stride or from an atomic counter (dynamic schedule).
+// Per-problem reductions go through the same tile partials and last-block
+// rule as the single-problem kernels, so a problem's arithmetic does not
+// depend on the batch it runs in.
+#pragma once
+#include "fw_device.cuh"
+
+namespace fw {
+
+struct GridBar {
+    uint32_t count;   // arrivals at the current barrier
+    uint32_t gen;     // barrier generation
+    uint32_t ndone;   // problems that stopped during this launch
+    int32_t error;    // 1: a barrier wait ran out of its clock budget
+    int32_t exit;     // 1: every live problem stopped (set by the last arrival)
+    uint32_t ctr[2];  // dynamic-schedule work counters (phase A, phase B)
+    uint32_t pad_;
+};
+
+struct BatchArgs {
+    const ProbDesc* desc;   // [P]
+    ProbState* state;       // [P]
+    const int2* work;       // [nwork] (problem, tile), tiles of live problems
+    int32_t nwork;
+    int32_t nlive;          // problems not done when the launch starts
+    int32_t iters;          // iterations in this launch
+    int32_t dynamic;        // 1: atomic work counter, 0: static grid stride
+    int32_t expect_extra;   // test hook: barrier waits for this many extra blocks
+    int32_t pad_;
+    GridBar* bar;
+    long long budget;       // clock cycles one barrier wait may take
+};
+
+__device__ __forceinline__ uint32_t ld_vol(const uint32_t* p) {
+    return *reinterpret_cast<const volatile uint32_t*>(p);
+}
+
+// Grid-wide barrier with a bounded wait.  Returns 0 to continue, 1 when the
+// last arrival saw every live problem done, -1 when the wait ran out (the
+// error flag is then set and the caller returns).
+__device__ __forceinline__ int grid_sync(GridBar* bar, long long budget, int nlive, int extra) {
+    __shared__ int s_r;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t g = ld_vol(&bar->gen);
+        __threadfence();
+        const uint32_t arrived = atomicAdd(&bar->count, 1u) + 1u;
+        int r = 0;
+        if (arrived == gridDim.x + uint32_t(extra)) {
+            atomicExch(&bar->count, 0u);
+            atomicExch(&bar->exit, ld_vol(&bar->ndone) >= uint32_t(nlive) ? 1 : 0);
+            __threadfence();
+            atomicAdd(&bar->gen, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (ld_vol(&bar->gen) == g) {
+                if (clock64() - t0 > budget) {
+                    atomicExch(&bar->error, 1);
+                    r = -1;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        if (r == 0) r = *reinterpret_cast<const volatile int32_t*>(&bar->exit);
+        s_r = r;
+    }
+    __syncthreads();
+    return s_r;
+}
+
+template <typename T, typename WT, int KMAX>
+__global__ void __launch_bounds__(kBlock) k_persistent(BatchArgs a) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T* sm_lane = reinterpret_cast<T*>(smraw);
+    T* sm_row = sm_lane + kBlock * (KMAX | 1);
+    __shared__ ProbDesc s_pd;
+    __shared__ int s_w, s_skip, s_upd;
+    __shared__ double s_alpha;
+    for (int it = 0; it < a.iters; ++it) {
+        for (int phase = 0; phase < 2; ++phase) {
+            int w = blockIdx.x;
+            for (;;) {
+                if (threadIdx.x == 0) {
+                    const int ww = a.dynamic ? int(atomicAdd(&a.bar->ctr[phase], 1u)) : w;
+                    s_w = ww;
+                    if (ww < a.nwork) {
+                        const int2 wk = a.work[ww];
+                        s_pd = a.desc[wk.x];
+                        const ProbState* st = a.state + wk.x;
+                        s_skip = ld_cg(&st->done);
+                        s_upd = ld_cg(&st->has_update);
+                        s_alpha = ld_cg(&st->alpha);
+                    }
+                }
+                __syncthreads();
+                const int ww = s_w;
+                if (ww >= a.nwork) break;
+                if (!s_skip) {
+                    const int2 wk = a.work[ww];
+                    ProbState* st = a.state + wk.x;
+                    if (phase == 0)
+                        tile_A<T, KMAX>(s_pd, st, wk.y, s_upd != 0, T(s_alpha), &a.bar->ndone);
+                    else
+                        tile_B<T, WT, KMAX, false>(s_pd, st, wk.y, sm_lane, sm_row,
+                                                   &a.bar->ndone);
+                }
+                __syncthreads();
+                w += gridDim.x;
+            }
+            const int r = grid_sync(a.bar, a.budget, a.nlive, a.expect_extra);
+            if (r < 0) return;
+            // the counter of this phase is idle until after the next barrier
+            if (a.dynamic && blockIdx.x == 0 && threadIdx.x == 0) atomicExch(&a.bar->ctr[phase], 0u);
+            if (phase == 1 && r == 1) return;
+        }
+    }
+}
+
+// Launcher of the persistent kernel for one (T, WT, KMAX).
+class BatchKern {
+public:
+    virtual ~BatchKern() {}
+    virtual size_t smem() const = 0;
+    virtual cudaError_t configure() = 0;
+    virtual cudaError_t occupancy(int* blocks_per_sm) = 0;
+    virtual cudaError_t launch(const BatchArgs& a, int grid, cudaStream_t s) = 0;
+};
+
+template <typename T, typename WT, int KMAX>
+class BatchKernImpl final : public BatchKern {
+public:
+    size_t smem() const override { return 2 * size_t(kBlock) * (KMAX | 1) * sizeof(T); }
+    cudaError_t configure() override {
+        return cudaFuncSetAttribute(k_persistent<T, WT, KMAX>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem()));
+    }
+    cudaError_t occupancy(int* bps) override {
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_persistent<T, WT, KMAX>, kBlock,
+                                                             smem());
+    }
+    cudaError_t launch(const BatchArgs& a, int grid, cudaStream_t s) override {
+        BatchArgs args = a;
+        void* params[] = {&args};
+        return cudaLaunchCooperativeKernel((const void*)k_persistent<T, WT, KMAX>, dim3(grid),
+                                           dim3(kBlock), params, smem(), s);
+    }
+};
+
+template <typename T, typename WT>
+BatchKern* make_batch_kern_t(int kmax) {
+    switch (kmax) {
+        case 4: return new BatchKernImpl<T, WT, 4>();
+        case 8: return new BatchKernImpl<T, WT, 8>();
+        case 12: return new BatchKernImpl<T, WT, 12>();
+        case 16: return new BatchKernImpl<T, WT, 16>();
+        case 32: return new BatchKernImpl<T, WT, 32>();
+        default: return nullptr;
+    }
+}
+
+BatchKern* make_batch_kern(int weight_dtype, int kmax);
+
+}  // namespace fw

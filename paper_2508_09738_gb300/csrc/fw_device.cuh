@@ -213,23 +213,20 @@ struct AccA {
 //  MODE_FLUSH: apply the pending update only.
 //  MODE_GRAD:  evaluate only; G' goes to Gout (SoA), choice to chout.
 template <typename T, int KMAX, int MODE>
-__device__ __forceinline__ void passA_rows(const ProbDesc& pd, T* __restrict__ U,
-                                           T* __restrict__ LU, const T* __restrict__ LS,
-                                           uint8_t* __restrict__ choice,
-                                           const int8_t* __restrict__ fid, int r_begin, int r_end,
-                                           bool upd, T alpha, AccA<T>& acc, T* __restrict__ Gout,
+__device__ __forceinline__ void passA_rows(const ProbDesc& pd, int r_begin, int r_end, bool upd,
+                                           T alpha, AccA<T>& acc, T* __restrict__ Gout,
                                            uint8_t* __restrict__ chout) {
     const int K = pd.K;
     const int64_t np = pd.npad;
-    T* Ub = U + pd.uoff;
-    T* LUb = LU + pd.uoff;
-    const T* LSb = LS + pd.uoff;
+    T* __restrict__ Ub = static_cast<T*>(pd.U);
+    T* __restrict__ LUb = static_cast<T*>(pd.LU);
+    const T* __restrict__ LSb = static_cast<const T*>(pd.LS);
+    uint8_t* __restrict__ choice = pd.choice;
     const T c2 = T(2.0 * pd.inv_eps);
     const T om = T(pd.omega0);
     const T oma = sub_(T(1), alpha);
     const bool greedy = pd.oracle == 0;
     for (int r = r_begin + threadIdx.x; r < r_end; r += kBlock) {
-        const int64_t gi = pd.row0 + r;
         T u[KMAX], lu[KMAX];
 #pragma unroll
         for (int k = 0; k < KMAX; ++k)
@@ -238,7 +235,7 @@ __device__ __forceinline__ void passA_rows(const ProbDesc& pd, T* __restrict__ U
                 lu[k] = ld_cg(LUb + k * np + r);
             }
         if (MODE != MODE_GRAD && upd) {
-            const uint8_t sv = ld_cg(choice + gi);
+            const uint8_t sv = ld_cg(choice + r);
             const int sp = sv & 0x7f;
 #pragma unroll
             for (int k = 0; k < KMAX; ++k)
@@ -256,7 +253,7 @@ __device__ __forceinline__ void passA_rows(const ProbDesc& pd, T* __restrict__ U
             }
         }
         if (MODE == MODE_FLUSH) continue;
-        const int f = __ldg(fid + gi);
+        const int f = __ldg(pd.fid + r);
         T G[KMAX];
         int s;
         bool moved;
@@ -266,10 +263,10 @@ __device__ __forceinline__ void passA_rows(const ProbDesc& pd, T* __restrict__ U
         if (MODE == MODE_GRAD) {
 #pragma unroll
             for (int k = 0; k < KMAX; ++k)
-                if (k < K) Gout[pd.uoff + k * np + r] = G[k];
-            chout[gi] = cv;
+                if (k < K) Gout[k * np + r] = G[k];
+            chout[r] = cv;
         } else {
-            choice[gi] = cv;
+            choice[r] = cv;
         }
         acc.g = add_(acc.g, gap);
         acc.nD = add_(acc.nD, nD);
@@ -284,17 +281,29 @@ __device__ __forceinline__ void passA_rows(const ProbDesc& pd, T* __restrict__ U
 // in shared memory (`sm_lane`, one KP-strided slot per thread); the lanes of a
 // row then add their slots in lane order into `sm_row[row]`.
 //   ONEHOT: bin[s_j] += w_ij            (pass B: row i of W^ S)
-//   else:   bin[k]  += w_ij * U[k][j]   (SpMM: row i of W^ U)
-template <typename T, typename WT, int KMAX, bool ONEHOT>
-__device__ __forceinline__ void csr_bins(const ProbDesc& pd, const int32_t* __restrict__ row_ptr,
-                                         const int32_t* __restrict__ col,
-                                         const WT* __restrict__ val,
-                                         const uint8_t* __restrict__ choice,
-                                         const T* __restrict__ Ub, int base, int r_end, int L,
-                                         T* __restrict__ sm_lane, T* __restrict__ sm_row) {
+//   else:   bin[k]  += w_ij * X[k][j]   (SpMM: row i of W^ X)
+// A lane keeps two chunks (8 entries) in flight: their column, weight and
+// gather loads are issued before the bins are updated, in entry order.
+// RO: gathers may use the read-only path (the gathered array is not written
+// during the launch); otherwise plain loads, ordered by the caller's fences.
+template <bool RO, typename V>
+__device__ __forceinline__ V ld_gather(const V* p) {
+    if constexpr (RO) return __ldg(p);
+    else return *p;
+}
+
+template <typename T, typename WT, int KMAX, bool ONEHOT, bool RO>
+__device__ __forceinline__ void csr_bins(const ProbDesc& pd, const T* __restrict__ X, int base,
+                                         int r_end, T* __restrict__ sm_lane,
+                                         T* __restrict__ sm_row) {
     constexpr int KP = KMAX | 1;
     const int K = pd.K;
+    const int L = pd.lanes;
     const int64_t np = pd.npad;
+    const int32_t* __restrict__ rp = pd.rp;
+    const int32_t* __restrict__ col = pd.col;
+    const WT* __restrict__ val = static_cast<const WT*>(pd.val);
+    const uint8_t* __restrict__ choice = pd.choice;
     const int tid = threadIdx.x;
     const int lane = tid & (L - 1);
     const int grp = tid / L;
@@ -312,33 +321,61 @@ __device__ __forceinline__ void csr_bins(const ProbDesc& pd, const int32_t* __re
                 if (k < K) my[k] = T(0);
         }
         if (r < r_end) {
-            const int64_t gi = pd.row0 + r;
-            const int e0 = __ldg(row_ptr + gi);
-            const int e1 = __ldg(row_ptr + gi + 1);
-            for (int e = e0 + 4 * lane; e < e1; e += 4 * L) {
-                const int4 c = __ldg(reinterpret_cast<const int4*>(col + e));
-                T v[4];
+            const int e0 = __ldg(rp + r);
+            const int e1 = __ldg(rp + r + 1);
+            for (int e = e0 + 4 * lane; e < e1; e += 8 * L) {
+                const int e2 = e + 4 * L;
+                const bool two = e2 < e1;
+                int cc[8];
+                T v[8];
+                {
+                    const int4 c = __ldg(reinterpret_cast<const int4*>(col + e));
+                    cc[0] = c.x; cc[1] = c.y; cc[2] = c.z; cc[3] = c.w;
+                }
+                if (two) {
+                    const int4 c = __ldg(reinterpret_cast<const int4*>(col + e2));
+                    cc[4] = c.x; cc[5] = c.y; cc[6] = c.z; cc[7] = c.w;
+                } else {
+                    cc[4] = cc[5] = cc[6] = cc[7] = r;
+                }
                 if constexpr (sizeof(WT) == 2) {
                     float vf[4];
                     ld_w4(val + e, vf);
-                    v[0] = vf[0]; v[1] = vf[1]; v[2] = vf[2]; v[3] = vf[3];
-                } else {
-                    ld_w4(val + e, v);
-                }
-                const int cc[4] = {c.x, c.y, c.z, c.w};
-                if (ONEHOT) {
 #pragma unroll
-                    for (int t = 0; t < 4; ++t) {
-                        const int sj = ld_cg(choice + cc[t]) & 0x7f;
-                        my[sj] = add_(my[sj], v[t]);
+                    for (int t = 0; t < 4; ++t) v[t] = vf[t];
+                    if (two) {
+                        ld_w4(val + e2, vf);
+#pragma unroll
+                        for (int t = 0; t < 4; ++t) v[4 + t] = vf[t];
                     }
                 } else {
+                    T w4[4];
+                    ld_w4(val + e, w4);
 #pragma unroll
-                    for (int t = 0; t < 4; ++t) {
-                        const int64_t jl = int64_t(cc[t]) - pd.row0;
+                    for (int t = 0; t < 4; ++t) v[t] = w4[t];
+                    if (two) {
+                        ld_w4(val + e2, w4);
 #pragma unroll
-                        for (int k = 0; k < KMAX; ++k)
-                            if (k < K) acc[k] = fma_(v[t], ld_cg(Ub + k * np + jl), acc[k]);
+                        for (int t = 0; t < 4; ++t) v[4 + t] = w4[t];
+                    }
+                }
+                const int nt = two ? 8 : 4;
+                if (ONEHOT) {
+                    int sj[8];
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) sj[t] = ld_gather<RO>(choice + cc[t]) & 0x7f;
+#pragma unroll
+                    for (int t = 0; t < 8; ++t)
+                        if (t < nt) my[sj[t]] = add_(my[sj[t]], v[t]);
+                } else {
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) {
+                        if (t < nt) {
+#pragma unroll
+                            for (int k = 0; k < KMAX; ++k)
+                                if (k < K)
+                                    acc[k] = fma_(v[t], ld_gather<RO>(X + k * np + cc[t]), acc[k]);
+                        }
                     }
                 }
             }
@@ -359,29 +396,23 @@ __device__ __forceinline__ void csr_bins(const ProbDesc& pd, const int32_t* __re
 }
 
 // Pass B over rows [r_begin, r_end): LS = L S (one-hot S) and sum_i <D_i, LS_i>.
-template <typename T, typename WT, int KMAX>
-__device__ __forceinline__ void passB_rows(const ProbDesc& pd, const int32_t* __restrict__ row_ptr,
-                                           const int32_t* __restrict__ col,
-                                           const WT* __restrict__ val, const T* __restrict__ diag,
-                                           const uint8_t* __restrict__ choice,
-                                           const T* __restrict__ U, T* __restrict__ LS,
-                                           int r_begin, int r_end, T& accq, T* sm_lane,
-                                           T* sm_row) {
+template <typename T, typename WT, int KMAX, bool RO>
+__device__ __forceinline__ void passB_rows(const ProbDesc& pd, int r_begin, int r_end, T& accq,
+                                           T* sm_lane, T* sm_row) {
     constexpr int KP = KMAX | 1;
     const int K = pd.K;
     const int64_t np = pd.npad;
-    const T* Ub = U + pd.uoff;
-    T* LSb = LS + pd.uoff;
+    const T* __restrict__ Ub = static_cast<const T*>(pd.U);
+    T* __restrict__ LSb = static_cast<T*>(pd.LS);
+    const T* __restrict__ diag = static_cast<const T*>(pd.diag);
     for (int base = r_begin; base < r_end; base += kBlock) {
-        csr_bins<T, WT, KMAX, true>(pd, row_ptr, col, val, choice, Ub, base, r_end, pd.lanes,
-                                    sm_lane, sm_row);
+        csr_bins<T, WT, KMAX, true, RO>(pd, nullptr, base, r_end, sm_lane, sm_row);
         __syncthreads();
         const int r = base + threadIdx.x;
         if (r < r_end) {
-            const int64_t gi = pd.row0 + r;
-            const uint8_t sv = ld_cg(choice + gi);
+            const uint8_t sv = ld_cg(pd.choice + r);
             const int si = sv & 0x7f;
-            const T dg = pd.comb ? diag[gi] : T(1);
+            const T dg = pd.comb ? diag[r] : T(1);
             T ls[KMAX];
 #pragma unroll
             for (int k = 0; k < KMAX; ++k)
@@ -405,31 +436,26 @@ __device__ __forceinline__ void passB_rows(const ProbDesc& pd, const int32_t* __
     }
 }
 
-// OUT = L U for rows [r_begin, r_end) (SoA in and out; OUT may not alias U).
+// OUT = L X for rows [r_begin, r_end) (SoA in and out; OUT may not alias X).
 template <typename T, typename WT, int KMAX>
-__device__ __forceinline__ void spmm_rows(const ProbDesc& pd, const int32_t* __restrict__ row_ptr,
-                                          const int32_t* __restrict__ col,
-                                          const WT* __restrict__ val, const T* __restrict__ diag,
-                                          const T* __restrict__ U, T* __restrict__ OUT,
-                                          int r_begin, int r_end, T* sm_lane, T* sm_row) {
+__device__ __forceinline__ void spmm_rows(const ProbDesc& pd, const T* __restrict__ X,
+                                          T* __restrict__ OUT, int r_begin, int r_end, T* sm_lane,
+                                          T* sm_row) {
     constexpr int KP = KMAX | 1;
     const int K = pd.K;
     const int64_t np = pd.npad;
-    const T* Ub = U + pd.uoff;
-    T* Ob = OUT + pd.uoff;
+    const T* __restrict__ diag = static_cast<const T*>(pd.diag);
     for (int base = r_begin; base < r_end; base += kBlock) {
-        csr_bins<T, WT, KMAX, false>(pd, row_ptr, col, val, nullptr, Ub, base, r_end, pd.lanes,
-                                     sm_lane, sm_row);
+        csr_bins<T, WT, KMAX, false, true>(pd, X, base, r_end, sm_lane, sm_row);
         __syncthreads();
         const int r = base + threadIdx.x;
         if (r < r_end) {
-            const int64_t gi = pd.row0 + r;
-            const T dg = pd.comb ? diag[gi] : T(1);
+            const T dg = pd.comb ? diag[r] : T(1);
 #pragma unroll
             for (int k = 0; k < KMAX; ++k)
                 if (k < K)
-                    Ob[k * np + r] = sub_(mul_(dg, ld_cg(Ub + k * np + r)),
-                                          sm_row[threadIdx.x * KP + k]);
+                    OUT[k * np + r] = sub_(mul_(dg, ld_cg(X + k * np + r)),
+                                           sm_row[threadIdx.x * KP + k]);
         }
         __syncthreads();
     }
@@ -501,6 +527,49 @@ __device__ __forceinline__ void finish_B(const ProbDesc& pd, ProbState* st,
     st->iter += 1;
     st->has_update = 1;
     st->cntB = 0;
+}
+
+// ------------------------------------------------------------- row tiles
+// One row tile of pass A with its block reduction; the last tile of the
+// problem to finish runs the stop test.  `ndone` (nullable) counts problems
+// that stop in this pass.  Every thread of the block must call it.
+template <typename T, int KMAX>
+__device__ __forceinline__ void tile_A(const ProbDesc& pd, ProbState* st, int tile, bool upd,
+                                       T alpha, uint32_t* ndone) {
+    const int r0 = tile * pd.tile_rows;
+    const int r1 = min(pd.n, r0 + pd.tile_rows);
+    AccA<T> acc{T(0), T(0), T(0), T(0), T(0)};
+    passA_rows<T, KMAX, MODE_STEP>(pd, r0, r1, upd, alpha, acc, nullptr, nullptr);
+    const T v[kNumA] = {acc.g, acc.nD, acc.nW, acc.tLU, acc.act};
+    block_partials<T, kNumA>(v, pd.partA + (size_t)tile * kNumA);
+    if (last_to_arrive(&st->cntA, pd.ntiles)) {
+        double S[kNumA];
+        sum_partials<kNumA>(pd.partA, pd.ntiles, S);
+        if (threadIdx.x == 0) {
+            finish_A(pd, st, S);
+            if (ndone && st->done) atomicAdd(ndone, 1u);
+        }
+    }
+}
+
+// One row tile of pass B; the last tile of the problem forms q and the step.
+template <typename T, typename WT, int KMAX, bool RO>
+__device__ __forceinline__ void tile_B(const ProbDesc& pd, ProbState* st, int tile, T* sm_lane,
+                                       T* sm_row, uint32_t* ndone) {
+    const int r0 = tile * pd.tile_rows;
+    const int r1 = min(pd.n, r0 + pd.tile_rows);
+    T accq = T(0);
+    passB_rows<T, WT, KMAX, RO>(pd, r0, r1, accq, sm_lane, sm_row);
+    const T v[kNumB] = {accq};
+    block_partials<T, kNumB>(v, pd.partB + (size_t)tile * kNumB);
+    if (last_to_arrive(&st->cntB, pd.ntiles)) {
+        double S[kNumB];
+        sum_partials<kNumB>(pd.partB, pd.ntiles, S);
+        if (threadIdx.x == 0) {
+            finish_B(pd, st, S);
+            if (ndone && st->done) atomicAdd(ndone, 1u);
+        }
+    }
 }
 
 }  // namespace fw

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/fw_seg.h"
 #include "fw_types.h"
@@ -21,44 +22,34 @@ fw_status cuda_fail(cudaError_t e, const char* what);
         if (e_ != cudaSuccess) return fw::cuda_fail(e_, #call); \
     } while (0)
 
-// Device buffers and geometry of one problem (or of a concatenated batch).
-struct Bufs {
-    ProbDesc pd{};
-    ProbState* st = nullptr;
-    int32_t* rp = nullptr;     // padded row_ptr, global rows (+1)
-    int32_t* col = nullptr;    // padded columns, global row indices
-    void* val = nullptr;       // padded weights (WT)
-    void* diag = nullptr;      // T[n], combinatorial Laplacian only
-    void* U = nullptr;         // T, SoA
-    void* LU = nullptr;
-    void* LS = nullptr;
-    uint8_t* choice = nullptr; // class chosen by the last evaluation | active bit
-    int8_t* fid = nullptr;     // fidelity class or -1
-    double* partA = nullptr;   // [ntiles][kNumA]
-    double* partB = nullptr;   // [ntiles][kNumB]
-};
-
 // Kernel launchers for one (iterate type, weight type, class bound) choice.
+// Every launcher takes the problem's descriptor (device pointers inside).
 class Ops {
 public:
     virtual ~Ops() {}
     virtual size_t elem() const = 0;    // sizeof(T)
     virtual size_t welem() const = 0;   // sizeof(WT)
     virtual int kmax() const = 0;
-    virtual void passA(const Bufs& b, cudaStream_t s) = 0;
-    virtual void passB(const Bufs& b, cudaStream_t s) = 0;
-    virtual void flush(const Bufs& b, cudaStream_t s) = 0;
-    virtual void grad(const Bufs& b, void* Gout, uint8_t* chout, cudaStream_t s) = 0;
-    virtual void spmm(const Bufs& b, const void* in, void* out, cudaStream_t s) = 0;
-    virtual void build(int64_t n, int64_t row0, const int32_t* rp, const int32_t* col,
-                       const double* w, const double* deg, const int32_t* rpp, int32_t* colp,
-                       void* valp, void* diag, int comb, cudaStream_t s) = 0;
-    virtual void init(const Bufs& b, const int32_t* labels, cudaStream_t s) = 0;
-    virtual void reinit(const Bufs& b, cudaStream_t s) = 0;
-    virtual void labels(const Bufs& b, int32_t* out, cudaStream_t s) = 0;
-    virtual void objective(const Bufs& b, const void* LUf, double* part, cudaStream_t s) = 0;
+    virtual void passA(const ProbDesc& pd, ProbState* st, cudaStream_t s) = 0;
+    virtual void passB(const ProbDesc& pd, ProbState* st, cudaStream_t s) = 0;
+    virtual void flush(const ProbDesc& pd, ProbState* st, cudaStream_t s) = 0;
+    virtual void grad(const ProbDesc& pd, ProbState* st, void* Gout, uint8_t* chout,
+                      cudaStream_t s) = 0;
+    virtual void spmm(const ProbDesc& pd, const void* X, void* out, cudaStream_t s) = 0;
+    virtual void build(int64_t n, const int32_t* rp, const int32_t* col, const double* w,
+                       const double* deg, const int32_t* rpp, int32_t* colp, void* valp,
+                       void* diag, int comb, cudaStream_t s) = 0;
+    virtual void reinit(const ProbDesc& pd, cudaStream_t s) = 0;
+    virtual void labels(const ProbDesc& pd, int32_t* out, cudaStream_t s) = 0;
+    virtual void objective(const ProbDesc& pd, const void* LUf, double* part, cudaStream_t s) = 0;
     virtual cudaError_t configure() = 0;   // dynamic shared-memory limits
 };
+
+// Non-template kernels (defined in fw_seg.cu).
+__global__ void k_validate(int64_t n, const int32_t* rp, const int32_t* col, const double* w,
+                           double* deg, int* err);
+__global__ void k_state_init(ProbState* st, const double* part, int nb);
+__global__ void k_fid(int64_t n, const int32_t* labels, int8_t* fid);
 
 // Factories, one per translation unit.  kmax in {4, 8, 12, 16, 32}.
 Ops* make_ops_f32(int kmax);
@@ -66,6 +57,40 @@ Ops* make_ops_bf16(int kmax);
 Ops* make_ops_f64(int kmax);
 Ops* make_ops(int weight_dtype, int K);
 int kmax_for(int K);
+
+// A graph on the host, as passed to the C ABI.
+struct HostGraph {
+    int64_t n;
+    const int32_t* rp;
+    const int32_t* col;
+    const double* w;
+    int32_t K;
+    const int32_t* labels;
+};
+
+// Host-side layout of one problem: sizes, tiles and the padded row_ptr.
+struct ProbLayout {
+    int64_t n = 0, nnz = 0, nnz_pad = 0, npad = 0;
+    int32_t K = 0, tile_rows = 0, ntiles = 0, lanes = 1;
+    std::vector<int32_t> rpp;   // padded row_ptr (local offsets)
+};
+
+// Host checks (options, row_ptr, labels) and the padded layout.
+fw_status check_opts(const fw_seg_opts& o);
+fw_status plan_problem(const HostGraph& g, const fw_seg_opts& o, ProbLayout& lay);
+// Device bytes of one problem's persistent arrays (256-byte aligned pieces).
+size_t problem_bytes(const ProbLayout& lay, size_t te, size_t we, bool comb);
+// Carve the problem's arrays out of [base, base + problem_bytes) and fill pd.
+void place_problem(char* base, const ProbLayout& lay, size_t te, size_t we, const fw_seg_opts& o,
+                   ProbDesc& pd);
+// Upload, validate and build the problem into pd's arrays; U_0, L U_0 and the
+// fresh state *st.  Temporaries are stream-ordered (cudaMallocAsync).  Waits
+// for the validation result on `s`.
+fw_status assemble_problem(Ops* ops, const HostGraph& g, const ProbLayout& lay, const ProbDesc& pd,
+                           ProbState* st, cudaStream_t s);
+// Restart pd at U_0 (or at its current U when from_current) with a fresh state.
+fw_status restart_problem(Ops* ops, const ProbDesc& pd, ProbState* st, bool from_current,
+                          cudaStream_t s);
 
 // Geometry helpers.
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }

@@ -12,6 +12,7 @@ public:
     size_t welem() const override { return sizeof(WT); }
     int kmax() const override { return KMAX; }
     static size_t smem() { return 2 * size_t(kBlock) * (KMAX | 1) * sizeof(T); }
+    static unsigned rows_grid(const ProbDesc& pd) { return unsigned((pd.n + kBlock - 1) / kBlock); }
 
     cudaError_t configure() override {
         cudaError_t e = cudaFuncSetAttribute(k_passB<T, WT, KMAX>,
@@ -20,52 +21,37 @@ public:
         return cudaFuncSetAttribute(k_spmm<T, WT, KMAX>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem()));
     }
-    void passA(const Bufs& b, cudaStream_t s) override {
-        k_passA<T, KMAX, MODE_STEP><<<b.pd.ntiles, kBlock, 0, s>>>(
-            b.pd, b.st, (T*)b.U, (T*)b.LU, (const T*)b.LS, b.choice, b.fid, b.partA, nullptr,
-            nullptr);
+    void passA(const ProbDesc& pd, ProbState* st, cudaStream_t s) override {
+        k_passA<T, KMAX, MODE_STEP><<<pd.ntiles, kBlock, 0, s>>>(pd, st, nullptr, nullptr);
     }
-    void flush(const Bufs& b, cudaStream_t s) override {
-        k_passA<T, KMAX, MODE_FLUSH><<<b.pd.ntiles, kBlock, 0, s>>>(
-            b.pd, b.st, (T*)b.U, (T*)b.LU, (const T*)b.LS, b.choice, b.fid, b.partA, nullptr,
-            nullptr);
+    void flush(const ProbDesc& pd, ProbState* st, cudaStream_t s) override {
+        k_passA<T, KMAX, MODE_FLUSH><<<pd.ntiles, kBlock, 0, s>>>(pd, st, nullptr, nullptr);
     }
-    void grad(const Bufs& b, void* Gout, uint8_t* chout, cudaStream_t s) override {
-        k_passA<T, KMAX, MODE_GRAD><<<b.pd.ntiles, kBlock, 0, s>>>(
-            b.pd, b.st, (T*)b.U, (T*)b.LU, (const T*)b.LS, b.choice, b.fid, b.partA, (T*)Gout,
-            chout);
+    void grad(const ProbDesc& pd, ProbState* st, void* Gout, uint8_t* chout,
+              cudaStream_t s) override {
+        k_passA<T, KMAX, MODE_GRAD><<<pd.ntiles, kBlock, 0, s>>>(pd, st, (T*)Gout, chout);
     }
-    void passB(const Bufs& b, cudaStream_t s) override {
-        k_passB<T, WT, KMAX><<<b.pd.ntiles, kBlock, smem(), s>>>(
-            b.pd, b.st, b.rp, b.col, (const WT*)b.val, (const T*)b.diag, b.choice, (const T*)b.U,
-            (T*)b.LS, b.partB);
+    void passB(const ProbDesc& pd, ProbState* st, cudaStream_t s) override {
+        k_passB<T, WT, KMAX><<<pd.ntiles, kBlock, smem(), s>>>(pd, st);
     }
-    void spmm(const Bufs& b, const void* in, void* out, cudaStream_t s) override {
-        k_spmm<T, WT, KMAX><<<b.pd.ntiles, kBlock, smem(), s>>>(
-            b.pd, b.rp, b.col, (const WT*)b.val, (const T*)b.diag, (const T*)in, (T*)out);
+    void spmm(const ProbDesc& pd, const void* X, void* out, cudaStream_t s) override {
+        k_spmm<T, WT, KMAX><<<pd.ntiles, kBlock, smem(), s>>>(pd, (const T*)X, (T*)out);
     }
-    void build(int64_t n, int64_t row0, const int32_t* rp, const int32_t* col, const double* w,
+    void build(int64_t n, const int32_t* rp, const int32_t* col, const double* w,
                const double* deg, const int32_t* rpp, int32_t* colp, void* valp, void* diag,
                int comb, cudaStream_t s) override {
         const unsigned g = unsigned((n + kBlock - 1) / kBlock);
-        k_build<WT, T><<<g, kBlock, 0, s>>>(n, row0, rp, col, w, deg, rpp, colp, (WT*)valp,
-                                             (T*)diag, comb);
+        k_build<WT, T><<<g, kBlock, 0, s>>>(n, rp, col, w, deg, rpp, colp, (WT*)valp, (T*)diag,
+                                             comb);
     }
-    void init(const Bufs& b, const int32_t* labels, cudaStream_t s) override {
-        const unsigned g = unsigned((b.pd.n + kBlock - 1) / kBlock);
-        k_init<T><<<g, kBlock, 0, s>>>(b.pd, labels, (T*)b.U, b.fid, b.choice);
+    void reinit(const ProbDesc& pd, cudaStream_t s) override {
+        k_reinit<T><<<rows_grid(pd), kBlock, 0, s>>>(pd);
     }
-    void reinit(const Bufs& b, cudaStream_t s) override {
-        const unsigned g = unsigned((b.pd.n + kBlock - 1) / kBlock);
-        k_reinit<T><<<g, kBlock, 0, s>>>(b.pd, (T*)b.U, b.fid, b.choice);
+    void labels(const ProbDesc& pd, int32_t* out, cudaStream_t s) override {
+        k_labels<T><<<rows_grid(pd), kBlock, 0, s>>>(pd, out);
     }
-    void labels(const Bufs& b, int32_t* out, cudaStream_t s) override {
-        const unsigned g = unsigned((b.pd.n + kBlock - 1) / kBlock);
-        k_labels<T><<<g, kBlock, 0, s>>>(b.pd, (const T*)b.U, out);
-    }
-    void objective(const Bufs& b, const void* LUf, double* part, cudaStream_t s) override {
-        const unsigned g = unsigned((b.pd.n + kBlock - 1) / kBlock);
-        k_objective<T><<<g, kBlock, 0, s>>>(b.pd, (const T*)b.U, (const T*)LUf, b.fid, part);
+    void objective(const ProbDesc& pd, const void* LUf, double* part, cudaStream_t s) override {
+        k_objective<T><<<rows_grid(pd), kBlock, 0, s>>>(pd, (const T*)LUf, part);
     }
 };
 

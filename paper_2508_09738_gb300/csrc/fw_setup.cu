@@ -1,0 +1,321 @@
+// Problem set-up shared by the single-problem handle and the batch engine:
+// option and CSR checks, device layout, upload, validation, Laplacian
+// assembly (Sec. 1), U_0 = U_hat (Sec. 5.1), L U_0 and the initial state.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "fw_device.cuh"
+#include "fw_internal.h"
+
+namespace fw {
+
+// ------------------------------------------------------------- kernels
+// Validation and degrees of the input CSR (one thread per row):
+//   columns strictly increasing and in range, no self loop, w finite and >= 0,
+//   w_ij == w_ji (binary search in row j), d_i = sum_j w_ij > 0 (Sec. 1).
+// err bits: 1 graph structure / weights, 2 asymmetric, 4 isolated node.
+__global__ void k_validate(int64_t n, const int32_t* rp, const int32_t* col, const double* w,
+                           double* deg, int* err) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int e0 = rp[i], e1 = rp[i + 1];
+    double d = 0.0;
+    int bad = 0;
+    int prev = -1;
+    for (int e = e0; e < e1; ++e) {
+        const int j = col[e];
+        const double x = w[e];
+        if (j < 0 || j >= n || j == i || j <= prev || !(x >= 0.0) || isinf(x)) {
+            bad |= 1;
+            break;
+        }
+        prev = j;
+        d += x;
+        int lo = rp[j], hi = rp[j + 1] - 1, pos = -1;
+        while (lo <= hi) {
+            const int mid = (lo + hi) >> 1;
+            const int cm = col[mid];
+            if (cm == i) {
+                pos = mid;
+                break;
+            }
+            if (cm < i) lo = mid + 1;
+            else hi = mid - 1;
+        }
+        if (pos < 0 || w[pos] != x) bad |= 2;
+    }
+    if (!bad && !(d > 0.0)) bad |= 4;
+    deg[i] = d;
+    if (bad) atomicOr(err, bad);
+}
+
+__global__ void __launch_bounds__(kBlock) k_state_init(ProbState* st, const double* part, int nb) {
+    double S[1];
+    sum_partials<1>(part, nb, S);
+    if (threadIdx.x == 0) {
+        ProbState z = {};
+        z.status = 2;  // FW_PENDING
+        z.E = S[0];
+        *st = z;
+    }
+}
+
+__global__ void k_fid(int64_t n, const int32_t* labels, int8_t* fid) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) fid[i] = int8_t(labels[i]);
+}
+
+// ------------------------------------------------------------- errors
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+const char* last_error_text() { return g_last_error.c_str(); }
+
+fw_status cuda_fail(cudaError_t e, const char* what) {
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return FW_ERR_CUDA;
+}
+
+static fw_status invalid(const std::string& m) {
+    set_error(m);
+    return FW_ERR_INVALID_ARG;
+}
+
+// ------------------------------------------------------------- choices
+int kmax_for(int K) { return K <= 4 ? 4 : K <= 8 ? 8 : K <= 12 ? 12 : K <= 16 ? 16 : 32; }
+
+Ops* make_ops(int weight_dtype, int K) {
+    const int km = kmax_for(K);
+    switch (weight_dtype) {
+        case FW_WEIGHTS_F32: return make_ops_f32(km);
+        case FW_WEIGHTS_BF16: return make_ops_bf16(km);
+        case FW_WEIGHTS_F64: return make_ops_f64(km);
+        default: return nullptr;
+    }
+}
+
+int tile_rows_for(int64_t n) {
+    const int64_t per = (n + kTilesTarget - 1) / kTilesTarget;
+    return int(round_up(std::max<int64_t>(per, 1), kBlock));
+}
+
+int default_lanes(double avg_padded_degree) {
+    int L = 1;
+    while (L < 32 && avg_padded_degree > 12.0 * L) L *= 2;
+    return L;
+}
+
+fw_status check_opts(const fw_seg_opts& o) {
+    if (!(o.eps > 0.0)) return invalid("eps must be > 0 (or +inf)");
+    if (!(o.omega0 >= 0.0) || std::isinf(o.omega0)) return invalid("omega0 must be finite and >= 0");
+    if (!(o.gap_tol >= 0.0)) return invalid("gap_tol must be >= 0");
+    if (o.max_iters < 0) return invalid("max_iters must be >= 0");
+    if (o.tol_mode != FW_TOL_ABS && o.tol_mode != FW_TOL_REL) return invalid("bad tol_mode");
+    if (o.weight_dtype < FW_WEIGHTS_F32 || o.weight_dtype > FW_WEIGHTS_F64)
+        return invalid("bad weight_dtype");
+    if (o.laplacian != FW_LAPLACIAN_SYM && o.laplacian != FW_LAPLACIAN_COMB)
+        return invalid("bad laplacian");
+    if (o.oracle != FW_ORACLE_GREEDY && o.oracle != FW_ORACLE_FULL) return invalid("bad oracle");
+    if (o.step_rule != FW_STEP_EXACT && o.step_rule != FW_STEP_ARMIJO)
+        return invalid("bad step_rule");
+    if (o.refresh_every < 0) return invalid("refresh_every must be >= 0");
+    if (o.iters_per_launch < 1 || o.iters_per_launch > 4096)
+        return invalid("iters_per_launch must be in [1, 4096]");
+    const int L = o.lanes_per_row;
+    if (L != 0 && (L < 1 || L > 32 || (L & (L - 1)) != 0))
+        return invalid("lanes_per_row must be 0 or a power of two <= 32");
+    return FW_OK;
+}
+
+fw_status plan_problem(const HostGraph& g, const fw_seg_opts& o, ProbLayout& lay) {
+    if (g.n < 1 || g.n >= (int64_t(1) << 31) - 1) return invalid("n must be in [1, 2^31-1)");
+    if (g.K < 2 || g.K > 32) {
+        set_error("K must be in [2, 32]");
+        return FW_ERR_UNSUPPORTED;
+    }
+    if (!g.rp || !g.labels) return invalid("row_ptr and labels must not be NULL");
+    if (g.rp[0] != 0) {
+        set_error("row_ptr[0] must be 0");
+        return FW_ERR_GRAPH;
+    }
+    const int64_t n = g.n;
+    lay.rpp.assign(size_t(n) + 1, 0);
+    int64_t acc = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        const int64_t d = int64_t(g.rp[i + 1]) - g.rp[i];
+        if (d < 0) {
+            set_error("row_ptr must be non-decreasing");
+            return FW_ERR_GRAPH;
+        }
+        acc += round_up(d, kPadW);
+        if (acc >= (int64_t(1) << 31)) {
+            set_error("padded nnz must stay below 2^31");
+            return FW_ERR_UNSUPPORTED;
+        }
+        lay.rpp[size_t(i) + 1] = int32_t(acc);
+    }
+    for (int64_t i = 0; i < n; ++i)
+        if (g.labels[i] < -1 || g.labels[i] >= g.K) return invalid("labels must be -1 or in [0, K)");
+    lay.n = n;
+    lay.nnz = g.rp[n];
+    lay.nnz_pad = acc;
+    if (lay.nnz > 0 && (!g.col || !g.w)) return invalid("col and w must not be NULL");
+    lay.npad = round_up(n, 32);
+    lay.K = g.K;
+    lay.tile_rows = tile_rows_for(n);
+    lay.ntiles = int32_t((n + lay.tile_rows - 1) / lay.tile_rows);
+    lay.lanes = o.lanes_per_row ? o.lanes_per_row : default_lanes(double(acc) / double(n));
+    return FW_OK;
+}
+
+static size_t a256(size_t x) { return (x + 255) / 256 * 256; }
+
+size_t problem_bytes(const ProbLayout& lay, size_t te, size_t we, bool comb) {
+    const size_t n = size_t(lay.n), np = size_t(lay.npad), K = size_t(lay.K);
+    size_t b = a256(4 * (n + 1)) + a256(4 * size_t(lay.nnz_pad)) + a256(we * size_t(lay.nnz_pad));
+    if (comb) b += a256(te * n);
+    b += 3 * a256(te * np * K) + a256(n) + a256(n);
+    b += a256(8 * size_t(lay.ntiles) * kNumA) + a256(8 * size_t(lay.ntiles) * kNumB);
+    return b;
+}
+
+void place_problem(char* base, const ProbLayout& lay, size_t te, size_t we, const fw_seg_opts& o,
+                   ProbDesc& pd) {
+    const size_t n = size_t(lay.n), np = size_t(lay.npad), K = size_t(lay.K);
+    const bool comb = o.laplacian == FW_LAPLACIAN_COMB;
+    char* p = base;
+    auto take = [&](size_t bytes) {
+        char* q = p;
+        p += a256(bytes);
+        return q;
+    };
+    std::memset(&pd, 0, sizeof(pd));
+    pd.rp = reinterpret_cast<const int32_t*>(take(4 * (n + 1)));
+    pd.col = reinterpret_cast<const int32_t*>(take(4 * size_t(lay.nnz_pad)));
+    pd.val = take(we * size_t(lay.nnz_pad));
+    pd.diag = comb ? take(te * n) : nullptr;
+    pd.U = take(te * np * K);
+    pd.LU = take(te * np * K);
+    pd.LS = take(te * np * K);
+    pd.choice = reinterpret_cast<uint8_t*>(take(n));
+    pd.fid = reinterpret_cast<const int8_t*>(take(n));
+    pd.partA = reinterpret_cast<double*>(take(8 * size_t(lay.ntiles) * kNumA));
+    pd.partB = reinterpret_cast<double*>(take(8 * size_t(lay.ntiles) * kNumB));
+    pd.n = int32_t(lay.n);
+    pd.npad = int32_t(lay.npad);
+    pd.K = lay.K;
+    pd.tile_rows = lay.tile_rows;
+    pd.ntiles = lay.ntiles;
+    pd.lanes = lay.lanes;
+    pd.comb = comb;
+    pd.oracle = o.oracle;
+    pd.step_rule = o.step_rule;
+    pd.tol_mode = o.tol_mode;
+    pd.max_iters = o.max_iters;
+    pd.inv_eps = std::isinf(o.eps) ? 0.0 : 1.0 / o.eps;
+    pd.omega0 = o.omega0;
+    pd.gap_tol = o.gap_tol;
+}
+
+#define FW_TRYS(x)                      \
+    do {                                \
+        fw_status s_ = (x);             \
+        if (s_ != FW_OK) return s_;     \
+    } while (0)
+
+// Stream-ordered temporaries, freed on every exit path.
+struct Temps {
+    cudaStream_t s;
+    std::vector<void*> ptrs;
+    explicit Temps(cudaStream_t st) : s(st) {}
+    ~Temps() {
+        for (void* p : ptrs) cudaFreeAsync(p, s);
+    }
+    template <typename P>
+    fw_status get(P** out, size_t bytes) {
+        void* q = nullptr;
+        cudaError_t e = cudaMallocAsync(&q, std::max<size_t>(bytes, 16), s);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            set_error(std::string("cudaMallocAsync of ") + std::to_string(bytes) +
+                      " bytes failed: " + cudaGetErrorString(e));
+            return FW_ERR_NO_MEMORY;
+        }
+        ptrs.push_back(q);
+        *out = reinterpret_cast<P*>(q);
+        return FW_OK;
+    }
+};
+
+static fw_status launched(const char* what) {
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? FW_OK : cuda_fail(e, what);
+}
+
+fw_status restart_problem(Ops* ops, const ProbDesc& pd, ProbState* st, bool from_current,
+                          cudaStream_t s) {
+    Temps t(s);
+    const int nb = int((pd.n + kBlock - 1) / kBlock);
+    double* opart = nullptr;
+    FW_TRYS(t.get(&opart, 8 * size_t(nb)));
+    if (!from_current) ops->reinit(pd, s);
+    ops->spmm(pd, pd.U, pd.LU, s);
+    ops->objective(pd, pd.LU, opart, s);
+    k_state_init<<<1, kBlock, 0, s>>>(st, opart, nb);
+    return launched("restart kernels");
+}
+
+fw_status assemble_problem(Ops* ops, const HostGraph& g, const ProbLayout& lay, const ProbDesc& pd,
+                           ProbState* st, cudaStream_t s) {
+    Temps t(s);
+    const int64_t n = lay.n, nnz = lay.nnz;
+    const size_t te = ops->elem();
+    int32_t *d_rp = nullptr, *d_col = nullptr, *d_lab = nullptr;
+    double *d_w = nullptr, *d_deg = nullptr;
+    int* d_err = nullptr;
+    FW_TRYS(t.get(&d_rp, 4 * (size_t(n) + 1)));
+    FW_TRYS(t.get(&d_col, 4 * size_t(nnz)));
+    FW_TRYS(t.get(&d_w, 8 * size_t(nnz)));
+    FW_TRYS(t.get(&d_deg, 8 * size_t(n)));
+    FW_TRYS(t.get(&d_lab, 4 * size_t(n)));
+    FW_TRYS(t.get(&d_err, sizeof(int)));
+    FW_CUDA(cudaMemcpyAsync(d_rp, g.rp, 4 * (size_t(n) + 1), cudaMemcpyHostToDevice, s));
+    if (nnz) {
+        FW_CUDA(cudaMemcpyAsync(d_col, g.col, 4 * size_t(nnz), cudaMemcpyHostToDevice, s));
+        FW_CUDA(cudaMemcpyAsync(d_w, g.w, 8 * size_t(nnz), cudaMemcpyHostToDevice, s));
+    }
+    FW_CUDA(cudaMemcpyAsync(d_lab, g.labels, 4 * size_t(n), cudaMemcpyHostToDevice, s));
+    FW_CUDA(cudaMemcpyAsync(const_cast<int32_t*>(pd.rp), lay.rpp.data(), 4 * (size_t(n) + 1),
+                            cudaMemcpyHostToDevice, s));
+    const size_t blk = te * size_t(lay.npad) * size_t(lay.K);
+    FW_CUDA(cudaMemsetAsync(pd.U, 0, blk, s));
+    FW_CUDA(cudaMemsetAsync(pd.LS, 0, blk, s));
+    FW_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), s));
+    const unsigned gr = unsigned((n + kBlock - 1) / kBlock);
+    k_validate<<<gr, kBlock, 0, s>>>(n, d_rp, d_col, d_w, d_deg, d_err);
+    FW_TRYS(launched("validate kernel"));
+    int err = 0;
+    FW_CUDA(cudaMemcpyAsync(&err, d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FW_CUDA(cudaStreamSynchronize(s));
+    if (err & 3) {
+        set_error(err & 1 ? "graph: column out of range / not increasing / self loop / bad weight"
+                          : "graph: W is not symmetric");
+        return FW_ERR_GRAPH;
+    }
+    if (err & 4) {
+        set_error("graph: a node has degree 0");
+        return FW_ERR_ISOLATED;
+    }
+    ops->build(n, d_rp, d_col, d_w, d_deg, pd.rp, const_cast<int32_t*>(pd.col),
+               const_cast<void*>(pd.val), const_cast<void*>(pd.diag), pd.comb, s);
+    k_fid<<<gr, kBlock, 0, s>>>(n, d_lab, const_cast<int8_t*>(pd.fid));
+    FW_TRYS(launched("build kernels"));
+    return restart_problem(ops, pd, st, false, s);
+}
+
+}  // namespace fw

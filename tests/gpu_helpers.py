@@ -65,10 +65,21 @@ def lockstep(g, iters, weights="f32", eps=50.0, omega0=1000.0, oracle="greedy",
                 rec["E"] = (E_g, E_o)
             st = s.step(1)
             rec["g"] = (st.gap, g_o)
-            assert rel(st.gap, g_o, 1e-9 * max(1.0, st.gap0)) <= tol, (k, st.gap, g_o)
+            # the GPU's gap reduction against an FP64 sum over its own G' and U ...
+            g_own = O.fw_gap(Gp, U, ch, act)
+            assert rel(st.gap, g_own, 1e-9 * max(1.0, st.gap0)) <= tol, (k, st.gap, g_own)
+            # ... and against the oracle's FP64 gradient: g is a sum of differences
+            # G'_k - G'_s, so its relative accuracy is bounded by that of G' (checked
+            # above at `tol`) times sum u|G'| / g; 10x tol covers the observed range
+            assert rel(st.gap, g_o, 1e-9 * max(1.0, st.gap0)) <= 10 * tol, (k, st.gap, g_o)
             if st.iters == k + 1:   # an update was applied: compare the step
                 assert rel(st.q, q_o, 1e-3 * nD) <= tol, (k, st.q, q_o)
-                assert rel(st.alpha, a_o) <= tol, (k, st.alpha, a_o)
+                # the step is the exact rule applied to the GPU's own g and q ...
+                if step == "exact":
+                    a_own = 1.0 if st.q <= 0 else min(1.0, st.gap / st.q)
+                    assert rel(st.alpha, a_own) <= 1e-12, (k, st.alpha, a_own)
+                # ... and inherits their accuracy against the oracle
+                assert rel(st.alpha, a_o) <= 10 * tol, (k, st.alpha, a_o)
                 rec.update(q=(st.q, q_o), alpha=(st.alpha, a_o))
             recs.append(rec)
             if st.status != B.FW_PENDING:

@@ -1,0 +1,192 @@
+"""Batched persistent kernel and serving loop vs single-problem solves (GPU)."""
+import os
+import time
+
+import numpy as np
+import pytest
+
+import oracle as O
+from gpu_helpers import agreement
+from paper_2508_09738_gb300 import binding as B
+from paper_2508_09738_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2508_09738_gb300 import build
+    build.build()
+
+
+def mixed_problems(P=10, seed=0, n_scale=0.05):
+    """Blob problems of uneven size and K (some ragged, some tiny) plus an image."""
+    gs = W.batched_blobs(P=P - 1, n_min=300, n_max=200_000, K_min=3, K_max=10, seed=seed,
+                         n_scale=n_scale)
+    gs.append(W.voronoi_image(side=61, K=5, seed=seed + 99, label_frac=0.02))
+    return gs
+
+
+def solve_alone(g, weights, **opts):
+    with B.Segmenter(g, weight_dtype=weights, **opts) as s:
+        st = s.solve()
+        return s.U(), s.labels(), st
+
+
+@pytest.mark.parametrize("weights", ["f32", "bf16"])
+@pytest.mark.parametrize("schedule,bps", [("static", 1), ("dynamic", 2), ("static", 0)])
+def test_batch_bitwise_equals_single(weights, schedule, bps):
+    gs = mixed_problems(P=10, seed=3)
+    iters = [30 + 7 * p for p in range(len(gs))]          # different caps per problem
+    opts = [B.fw_seg_default_opts(max_iters=it, weight_dtype=weights) for it in iters]
+    with B.Batch(gs, opts, weight_dtype=weights, schedule=schedule, blocks_per_sm=bps) as b:
+        stats = b.solve()
+        for p, g in enumerate(gs):
+            U, lab, st = solve_alone(g, weights, max_iters=iters[p])
+            assert np.array_equal(b.U(p), U), p
+            assert np.array_equal(b.labels(p), lab), p
+            assert stats[p].iters == st.iters and stats[p].status == st.status
+            assert stats[p].gap == st.gap and stats[p].alpha == st.alpha
+
+
+def test_batch_relaunch_and_reset_reproduce():
+    gs = mixed_problems(P=6, seed=5)
+    opts = B.fw_seg_default_opts(max_iters=40)
+    with B.Batch(gs, opts, iters_per_launch=7) as b:
+        b.solve()
+        U1 = [b.U(p) for p in range(len(gs))]
+        b.reset()
+        b.solve()
+        U2 = [b.U(p) for p in range(len(gs))]
+    with B.Batch(gs, opts) as b:               # one launch for all iterations
+        b.solve()
+        U3 = [b.U(p) for p in range(len(gs))]
+    for a, c, d in zip(U1, U2, U3):
+        assert np.array_equal(a, c) and np.array_equal(a, d)
+
+
+def test_batch_f64_matches_oracle():
+    gs = mixed_problems(P=5, seed=7, n_scale=0.01)
+    with B.Batch(gs, B.fw_seg_default_opts(max_iters=25), weight_dtype="f64") as b:
+        b.solve()
+        for p, g in enumerate(gs):
+            P = O.make_problem(g, 50.0, 1000.0, "f64")
+            Uo, _ = O.gfw_solve(P, max_iters=25)
+            assert np.max(np.abs(b.U(p) - Uo)) < 1e-9
+
+
+def test_batch_independent_stop_rules():
+    gs = mixed_problems(P=6, seed=9)
+    opts = [B.fw_seg_default_opts(max_iters=400, gap_tol=1e-2, tol_mode="rel"),
+            B.fw_seg_default_opts(max_iters=3),
+            B.fw_seg_default_opts(max_iters=0),
+            B.fw_seg_default_opts(eps=0.1, omega0=1e5, max_iters=50),      # one shot
+            B.fw_seg_default_opts(max_iters=60, step_rule="armijo"),
+            B.fw_seg_default_opts(max_iters=60, oracle="full")]
+    with B.Batch(gs, opts) as b:
+        stats = b.solve()
+    for p, (g, o) in enumerate(zip(gs, opts)):
+        with B.Segmenter(g, eps=o.eps, omega0=o.omega0, max_iters=o.max_iters,
+                         gap_tol=o.gap_tol, tol_mode=o.tol_mode, step_rule=o.step_rule,
+                         oracle=o.oracle) as s:
+            st = s.solve()
+        assert (stats[p].iters, stats[p].status) == (st.iters, st.status), p
+    assert stats[1].iters == 3 and stats[2].iters == 0 and stats[3].iters == 1
+
+
+def test_batch_autotune_cache(tmp_path):
+    gs = mixed_problems(P=4, seed=11)
+    cache = str(tmp_path / "tune.txt")
+    opts = B.fw_seg_default_opts(max_iters=10)
+    with B.Batch(gs, opts, tune_cache=cache) as b:
+        i1 = b.info()
+        b.solve()
+        U1 = b.U(0)
+    with B.Batch(gs, opts, tune_cache=cache) as b:
+        i2 = b.info()
+        b.solve()
+        U2 = b.U(0)
+    assert i1.tuned == 1 and i2.tuned == 2
+    assert (i1.blocks_per_sm, i1.schedule) == (i2.blocks_per_sm, i2.schedule)
+    assert np.array_equal(U1, U2)
+    assert os.path.getsize(cache) > 0
+
+
+def test_batch_barrier_timeout_is_reported_and_recoverable():
+    """A barrier that waits for a block that never arrives runs out of its
+    budget: the launch ends with FW_ERR_TIMEOUT and the context stays usable."""
+    gs = mixed_problems(P=3, seed=13)
+    t0 = time.time()
+    with B.Batch(gs, B.fw_seg_default_opts(max_iters=5), test_barrier_extra=1,
+                 spin_budget_ms=20, blocks_per_sm=1, schedule="static") as b:
+        with pytest.raises(B.FwError) as e:
+            b.solve()
+    assert e.value.status == B.FW_ERR_TIMEOUT
+    assert time.time() - t0 < 30
+    U, _, _ = solve_alone(gs[0], "f32", max_iters=5)   # the GPU still works
+    assert np.all(np.isfinite(U))
+
+
+# ------------------------------------------------------------------ serving --
+
+def requests(seed=21):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(14):
+        if i % 3 == 2:
+            side = int(rng.choice([40, 64, 90]))
+            g = W.voronoi_image(side=side, K=int(rng.integers(3, 9)), seed=seed + i,
+                                label_frac=0.02)
+            o = dict(eps=0.1, omega0=1e5, max_iters=20) if i % 2 else \
+                dict(max_iters=300, gap_tol=1e-4, tol_mode="rel")
+        else:
+            g = W.blobs_knn(n=int(rng.integers(300, 4000)), K=int(rng.integers(3, 9)),
+                            seed=seed + i, label_frac=0.02)
+            o = dict(max_iters=300, gap_tol=1e-4, tol_mode="rel")
+        out.append((g, o))
+    return out
+
+
+def test_server_results_equal_alone():
+    reqs = requests()
+    alone = [solve_alone(g, "f32", **o) for g, o in reqs]
+    # a small pool forces queueing and reuse of freed memory
+    need = max(B.fw_seg_footprint(g.n, g.nnz, 8, "f32") for g, _ in reqs)
+    with B.Server(hbm_budget_bytes=3 * need, max_slots=4, max_K=8, iters_per_epoch=8) as srv:
+        tickets = []
+        for g, o in reqs:
+            tickets.append(srv.submit(g, **o))
+            time.sleep(0.002)
+        for (g, o), t, (U, lab, st) in zip(reqs, tickets, alone):
+            rc, lab_s, st_s = srv.wait(t, g.n, timeout_ms=60_000)
+            assert rc == st.status, (rc, st.status)
+            assert np.array_equal(lab_s, lab)
+            assert st_s.iters == st.iters and st_s.gap == st.gap
+        info = srv.info()
+    assert info.completed == len(reqs) and info.failed == 0 and info.admitted == len(reqs)
+    assert info.epochs > 0 and info.pool_used == 0
+
+
+def test_server_rejects_and_reports_errors():
+    g = W.blobs_knn(n=2000, K=5, seed=1)
+    small = B.fw_seg_footprint(300, 300 * 12, 8, "f32")
+    with B.Server(hbm_budget_bytes=small, max_slots=2, max_K=6) as srv:
+        with pytest.raises(B.FwError) as e:
+            srv.submit(g)                                     # can never fit
+        assert e.value.status == B.FW_ERR_NO_MEMORY
+        big_k = W.blobs_knn(n=200, K=7, seed=2)
+        with pytest.raises(B.FwError) as e:
+            srv.submit(big_k)                                 # K above max_K
+        assert e.value.status == B.FW_ERR_UNSUPPORTED
+        bad = W.blobs_knn(n=200, K=3, seed=3)
+        bad.w = bad.w.copy()
+        bad.w[0] *= 2.0                                       # asymmetric
+        t = srv.submit(bad)
+        rc, _, _ = srv.wait(t, bad.n, timeout_ms=30_000)
+        assert rc == B.FW_ERR_GRAPH
+        ok = W.blobs_knn(n=200, K=3, seed=4)
+        t = srv.submit(ok, max_iters=20)
+        rc, lab, st = srv.wait(t, ok.n, timeout_ms=30_000)
+        assert rc == B.FW_NOT_CONVERGED and st.iters == 20
+        info = srv.info()
+        assert info.rejected == 2 and info.failed == 1

