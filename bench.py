@@ -186,6 +186,24 @@ def config_dict(args, c, g, iters):
             "parallelism": f"replicas x{args.gpus}"}
 
 
+# ----------------------------------------------------------- multi-rank --
+def max_over_ranks(x: float, device: str) -> float:
+    """Max of a per-rank scalar over all ranks (identity without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, seconds_local: float, world: int, device: str) -> tuple:
+    """(rate, seconds): units of all ranks / the slowest rank's time (weak scaling)."""
+    sec = max_over_ranks(seconds_local, device)
+    return world * units_per_rank / sec, sec
+
+
 # ------------------------------------------------------------------ ours --
 def main():
     args = parse()
@@ -245,14 +263,12 @@ def main():
     torch.cuda.synchronize()
     clk = clocks.stop()
     t_ms = sum(a.elapsed_time(b) for a, b in ev)
+    value, t_s = whole_job_rate(args.steps * stats.iters, t_ms / 1000.0, world, "cuda")
+    t_ms = 1000.0 * t_s
     if world > 1:
-        t = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_ms = float(t.item())
         dist.barrier()
     labels = seg.labels()
-    value = world * args.steps * stats.iters / (t_ms / 1000.0)
-    solves = world * args.steps / (t_ms / 1000.0)
+    solves = world * args.steps / t_s
 
     # per-pass device times (CUDA events on the solver's stream) -> roofline
     seg.reset()
@@ -299,11 +315,8 @@ def main():
             B.fw_seg_destroy(h)
             it_e2e += st.iters
         dt = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([dt], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
-        e2e = {"value": world * it_e2e / dt, "unit": "iter/s",
+        e2e_rate, dt = whole_job_rate(it_e2e, dt, world, "cuda")
+        e2e = {"value": e2e_rate, "unit": "iter/s",
                "h2d_bytes_per_step": int(4 * (g.n + 1) + 12 * g.nnz + 4 * g.n),
                "d2h_bytes_per_step": int(4 * g.n),
                "steps": steps_e2e, "includes": "create (H2D, validation, Laplacian assembly, "
