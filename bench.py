@@ -204,13 +204,218 @@ def whole_job_rate(units_per_rank: float, seconds_local: float, world: int, devi
     return world * units_per_rank / sec, sec
 
 
+# --------------------------------------------------------------- batched --
+def run_batched(args, rank, world, local):
+    """256 uneven blob problems in one persistent launch vs 256 sequential solves."""
+    import torch
+    from paper_2508_09738_gb300 import binding as B
+    from paper_2508_09738_gb300 import build as Bld
+    torch.cuda.set_device(local)
+    Bld.build()
+    P = 256
+    t0 = time.time()
+    gs = W.batched_blobs(P=P, n_min=1000, n_max=200_000, K_min=3, K_max=10, label_frac=0.02,
+                         seed=W.SEED0 + 3, device="cuda")
+    gen_s = time.time() - t0
+    iters = args.iters or 200
+    weights = args.weights or "bf16"
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    opts = B.fw_seg_default_opts(max_iters=iters, weight_dtype=weights)
+    cache = os.environ.get("FW_TUNE_CACHE") or os.path.join(tempfile.gettempdir(), "fwseg_tune.txt")
+    t0 = time.time()
+    bt = B.Batch(gs, opts, weight_dtype=weights, cuda_stream=stream.cuda_stream, tune_cache=cache)
+    create_s = time.time() - t0
+    info = bt.info().as_dict()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def timed(fn, steps):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        out = None
+        for s_ in range(steps):
+            flush.zero_()
+            ev[s_][0].record(stream)
+            out = fn()
+            ev[s_][1].record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev) / 1000.0, out
+
+    def batched_step():
+        bt.reset()
+        return bt.solve()
+
+    for _ in range(args.warmup):
+        batched_step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    t_b, stats = timed(batched_step, args.steps)
+    clk = clocks.stop()
+    total_iters = sum(s_.iters for s_ in stats)
+    # the plain one-problem-at-a-time path on the same problems, resident on the device
+    segs = [B.Segmenter(g, max_iters=iters, weight_dtype=weights, iters_per_launch=iters,
+                        cuda_stream=stream.cuda_stream) for g in gs]
+
+    def sequential_step():
+        it = 0
+        for sg in segs:
+            sg.reset()
+            it += sg.solve().iters
+        return it
+
+    sequential_step()
+    steps_seq = max(1, min(args.steps, 2))
+    t_s, it_seq = timed(sequential_step, steps_seq)
+    same = all(np.array_equal(bt.labels(p), segs[p].labels()) for p in range(P))
+    for sg in segs:
+        sg.close()
+    wb = {"f32": 4, "bf16": 2, "f64": 8}[weights]
+    byt = sum(bytes_per_unit(g.n, g.nnz, g.K, wb)["iteration"] * st.iters
+              for g, st in zip(gs, stats))
+    peaks = load_peaks()
+    achieved = byt * args.steps / t_b / 1e9
+    line = {
+        "metric": "FW iters/s", "value": total_iters * args.steps / t_b, "unit": "iter/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * t_b / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "batched256", "problems": P, "rows": sum(g.n for g in gs),
+                   "nnz": sum(g.nnz for g in gs), "K": "3..10", "iters_per_solve": iters,
+                   "weights": weights, "eps": 50.0, "omega0": 1000.0,
+                   "l2": "256 MiB buffer written between timed steps"},
+        "solves_per_s": P * args.steps / t_b,
+        "sequential_plain": {"iters_per_s": it_seq * steps_seq / t_s,
+                             "solves_per_s": P * steps_seq / t_s,
+                             "ms_per_step": 1000 * t_s / steps_seq},
+        "speedup_vs_sequential": (P * args.steps / t_b) / (P * steps_seq / t_s),
+        "labels_equal_to_single": same, "batch_info": info, "clocks": clk,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                     "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                     "kernel": "k_persistent", "peak_source": peaks["source"],
+                     "algorithmic_bytes": "sum over problems of iteration bytes x iterations"},
+        "setup_s": {"generate": gen_s, "create_and_tune": create_s},
+    }
+    bt.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------- serving --
+def run_serving(args, rank, world, local):
+    """Poisson requests at swept rates: continuous batching vs sequential solves."""
+    import torch
+    from paper_2508_09738_gb300 import binding as B
+    from paper_2508_09738_gb300 import build as Bld
+    torch.cuda.set_device(local)
+    Bld.build()
+    rng = np.random.default_rng(W.SEED0 + 4)
+    pool = []
+    t0 = time.time()
+    for i in range(12):
+        n = int(round(np.exp(rng.uniform(np.log(1e3), np.log(2e5)))))
+        K = int(rng.integers(3, 9))
+        g = W.blobs_knn(n=max(n, 4 * K), K=K, label_frac=0.02, seed=W.SEED0 + 400 + i,
+                        device="cuda")
+        pool.append((g, dict(eps=50.0, omega0=1000.0)))
+    for i in range(12):
+        side = int(rng.choice([256, 512, 768, 1024]))
+        K = int(rng.integers(3, 9))
+        g = W.voronoi_image(side=side, K=K, label_frac=0.005, seed=W.SEED0 + 500 + i)
+        pool.append((g, dict(eps=50.0, omega0=1e5)))
+    gen_s = time.time() - t0
+    common = dict(gap_tol=1e-4, tol_mode="rel", max_iters=2000, weight_dtype="f32")
+
+    def plain(g, o):
+        with B.Segmenter(g, iters_per_launch=64, **o, **common) as sg:
+            st = sg.solve()
+            return sg.labels(), st
+
+    for g, o in pool[:3]:
+        plain(g, o)
+    service = []
+    alone = []
+    for g, o in pool:
+        t = time.perf_counter()
+        lab, st = plain(g, o)
+        service.append(time.perf_counter() - t)
+        alone.append((lab, st.iters))
+    cap = 1.0 / float(np.mean(service))
+    budget = 16 << 30
+    R = args.steps * 20
+    rates = []
+    with B.Server(hbm_budget_bytes=budget, max_slots=32, max_K=8, iters_per_epoch=16,
+                  weight_dtype="f32") as srv:
+        for mult in (0.5, 1.0, 2.0):
+            lam = mult * cap
+            arr = np.cumsum(rng.exponential(1.0 / lam, size=R))
+            pick = rng.integers(0, len(pool), size=R)
+            # served: submit on schedule, poll for completions
+            lat, t_start = [], time.perf_counter()
+            pending = {}
+            i = 0
+            equal = True
+            while i < R or pending:
+                now = time.perf_counter() - t_start
+                while i < R and arr[i] <= now:
+                    g, o = pool[pick[i]]
+                    pending[srv.submit(g, **o, **common)] = (i, arr[i])
+                    i += 1
+                for tk in list(pending):
+                    idx, ta = pending[tk]
+                    g, _ = pool[pick[idx]]
+                    rc, lab, st = srv.poll(tk, g.n)
+                    if rc != B.FW_PENDING:
+                        lat.append(time.perf_counter() - t_start - ta)
+                        equal &= bool(np.array_equal(lab, alone[pick[idx]][0]))
+                        del pending[tk]
+                time.sleep(0.0005)
+            span_srv = time.perf_counter() - t_start
+            # sequential plain solves of the same arrival process
+            lat_seq, t_start = [], time.perf_counter()
+            for j in range(R):
+                now = time.perf_counter() - t_start
+                if now < arr[j]:
+                    time.sleep(arr[j] - now)
+                g, o = pool[pick[j]]
+                plain(g, o)
+                lat_seq.append(time.perf_counter() - t_start - arr[j])
+            span_seq = time.perf_counter() - t_start
+            rates.append({
+                "rate_per_s": lam, "x_capacity": mult, "requests": R,
+                "served": {"solves_per_s": R / span_srv, "p50_ms": 1e3 * np.percentile(lat, 50),
+                           "p99_ms": 1e3 * np.percentile(lat, 99)},
+                "sequential": {"solves_per_s": R / span_seq,
+                               "p50_ms": 1e3 * np.percentile(lat_seq, 50),
+                               "p99_ms": 1e3 * np.percentile(lat_seq, 99)},
+                "labels_equal_to_alone": equal})
+        info = srv.info().as_dict()
+    best = max(rates, key=lambda r: r["served"]["solves_per_s"])
+    line = {
+        "metric": "solves/s", "value": best["served"]["solves_per_s"], "unit": "solves/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": 3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "serving", "pool": "12 blob graphs (n 1e3..2e5) + 12 Voronoi "
+                   "images (256^2..1024^2), K 3..8", "stop": "gap <= 1e-4 g_0, cap 2000",
+                   "hbm_budget_bytes": budget, "max_slots": 32, "iters_per_epoch": 16},
+        "sequential_capacity_per_s": cap, "rates": rates, "server": info,
+        "setup_s": {"generate": gen_s},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------------ ours --
 def main():
     args = parse()
-    c = W.CONFIGS[args.workload]
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.workload == "batched256":
+        return run_batched(args, rank, world, local)
+    if args.workload == "serving":
+        return run_serving(args, rank, world, local)
+    c = W.CONFIGS[args.workload]
     if args.impl == "reference":
         run_reference(args, c, rank)
         return

@@ -76,12 +76,17 @@ __device__ __forceinline__ int grid_sync(GridBar* bar, long long budget, int nli
 
 template <typename T, typename WT, int KMAX>
 __global__ void __launch_bounds__(kBlock) k_persistent(BatchArgs a) {
-    extern __shared__ __align__(16) unsigned char smraw[];
+    extern __shared__ __align__(128) unsigned char smraw[];
     T* sm_lane = reinterpret_cast<T*>(smraw);
     T* sm_row = sm_lane + kBlock * (KMAX | 1);
+    T* stage = reinterpret_cast<T*>(smraw);        // phases A and B use the buffer in turn
     __shared__ ProbDesc s_pd;
     __shared__ int s_w, s_skip, s_upd;
-    __shared__ double s_alpha;
+    __shared__ T s_alpha;
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    uint32_t mb_phase = 0;   // parity of the bulk-copy mbarrier
     for (int it = 0; it < a.iters; ++it) {
         for (int phase = 0; phase < 2; ++phase) {
             int w = blockIdx.x;
@@ -95,7 +100,7 @@ __global__ void __launch_bounds__(kBlock) k_persistent(BatchArgs a) {
                         const ProbState* st = a.state + wk.x;
                         s_skip = ld_cg(&st->done);
                         s_upd = ld_cg(&st->has_update);
-                        s_alpha = ld_cg(&st->alpha);
+                        s_alpha = alpha_of<T>(st);
                     }
                 }
                 __syncthreads();
@@ -105,7 +110,8 @@ __global__ void __launch_bounds__(kBlock) k_persistent(BatchArgs a) {
                     const int2 wk = a.work[ww];
                     ProbState* st = a.state + wk.x;
                     if (phase == 0)
-                        tile_A<T, KMAX>(s_pd, st, wk.y, s_upd != 0, T(s_alpha), &a.bar->ndone);
+                        tile_A<T, KMAX>(s_pd, st, wk.y, s_upd != 0, s_alpha, &a.bar->ndone, stage,
+                                        &bar, mb_phase);
                     else
                         tile_B<T, WT, KMAX, false>(s_pd, st, wk.y, sm_lane, sm_row,
                                                    &a.bar->ndone);
@@ -135,7 +141,11 @@ public:
 template <typename T, typename WT, int KMAX>
 class BatchKernImpl final : public BatchKern {
 public:
-    size_t smem() const override { return 2 * size_t(kBlock) * (KMAX | 1) * sizeof(T); }
+    size_t smem() const override {
+        const size_t b = 2 * size_t(kBlock) * (KMAX | 1) * sizeof(T);
+        const size_t a = 3 * size_t(kBlock) * KMAX * sizeof(T);
+        return a > b ? a : b;
+    }
     cudaError_t configure() override {
         return cudaFuncSetAttribute(k_persistent<T, WT, KMAX>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem()));

@@ -41,26 +41,122 @@ template <> __device__ __forceinline__ double inf_<double>() { return CUDART_INF
 
 // ------------------------------------------------------------ weight loads
 // Four consecutive entries of a padded CSR row (start is a multiple of 4).
+__device__ __forceinline__ int4 ld_stream(const int4* p);
+__device__ __forceinline__ float4 ld_stream(const float4* p);
+__device__ __forceinline__ uint2 ld_stream(const uint2* p);
+__device__ __forceinline__ double2 ld_stream(const double2* p);
+
 __device__ __forceinline__ void ld_w4(const float* p, float (&v)[4]) {
-    const float4 t = __ldg(reinterpret_cast<const float4*>(p));
+    const float4 t = ld_stream(reinterpret_cast<const float4*>(p));
     v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
 }
 __device__ __forceinline__ void ld_w4(const __nv_bfloat16* p, float (&v)[4]) {
     // bf16 is the upper half of an fp32 pattern: widening is a shift (exact)
-    const uint2 t = __ldg(reinterpret_cast<const uint2*>(p));
+    const uint2 t = ld_stream(reinterpret_cast<const uint2*>(p));
     v[0] = __uint_as_float(t.x << 16);
     v[1] = __uint_as_float(t.x & 0xffff0000u);
     v[2] = __uint_as_float(t.y << 16);
     v[3] = __uint_as_float(t.y & 0xffff0000u);
 }
 __device__ __forceinline__ void ld_w4(const double* p, double (&v)[4]) {
-    const double2 a = __ldg(reinterpret_cast<const double2*>(p));
-    const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+    const double2 a = ld_stream(reinterpret_cast<const double2*>(p));
+    const double2 b = ld_stream(reinterpret_cast<const double2*>(p) + 1);
     v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
 }
 
 // Plain (coherent) loads for data written inside a persistent launch.
 template <typename T> __device__ __forceinline__ T ld_cg(const T* p) { return __ldcg(p); }
+
+// Streaming loads that do not allocate in L1 (CSR columns and weights), so
+// that the gathered class bytes keep their L1 lines.
+__device__ __forceinline__ int4 ld_stream(const int4* p) {
+    int4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.s32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ float4 ld_stream(const float4* p) {
+    float4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ uint2 ld_stream(const uint2* p) {
+    uint2 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v2.u32 {%0, %1}, [%2];"
+                 : "=r"(v.x), "=r"(v.y) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ double2 ld_stream(const double2* p) {
+    double2 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v2.f64 {%0, %1}, [%2];"
+                 : "=d"(v.x), "=d"(v.y) : "l"(p));
+    return v;
+}
+
+// Per-iteration constants in the iterate type (precomputed on the host, so
+// the kernels do no FP64 work per thread in the FP32 path).
+template <typename T> __device__ __forceinline__ T c2_of(const ProbDesc& pd);
+template <> __device__ __forceinline__ float c2_of<float>(const ProbDesc& pd) { return pd.c2f; }
+template <> __device__ __forceinline__ double c2_of<double>(const ProbDesc& pd) { return pd.c2; }
+template <typename T> __device__ __forceinline__ T om_of(const ProbDesc& pd);
+template <> __device__ __forceinline__ float om_of<float>(const ProbDesc& pd) { return pd.omf; }
+template <> __device__ __forceinline__ double om_of<double>(const ProbDesc& pd) { return pd.omega0; }
+template <typename T> __device__ __forceinline__ T alpha_of(const ProbState* st);
+template <> __device__ __forceinline__ float alpha_of<float>(const ProbState* st) {
+    return __ldcg(&st->alpha_f);
+}
+template <> __device__ __forceinline__ double alpha_of<double>(const ProbState* st) {
+    return __ldcg(&st->alpha);
+}
+
+// ------------------------------------------------ bulk async copies (TMA)
+// 1-D cp.async.bulk global -> shared completing on an mbarrier.  Addresses
+// and sizes must be multiples of 16 bytes; callers guarantee it.
+constexpr long long kMbarSpins = 1ll << 26;   // bound of one mbarrier wait (seconds)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the phase of the given parity; false when the bound ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    for (long long i = 0; i < kMbarSpins; ++i) {
+        if (mbar_test(bar, parity)) return true;
+        if (i > 8) __nanosleep(40);
+    }
+    return false;
+}
 
 // ------------------------------------------------------- block reductions
 // Sum NQ per-thread values over the block: FP32 (or FP64) butterfly inside each
@@ -103,11 +199,12 @@ __device__ __forceinline__ bool last_to_arrive(uint32_t* cnt, uint32_t total) {
 }
 
 // Fixed-order FP64 sum of ntiles partial records of NQ doubles (L2 loads).
-// Every thread of the block must call it; out[] is valid in all threads.
+// `scratch` is kBlock*NQ doubles of shared memory.  Every thread of the block
+// must call it; out[] is valid in all threads.
 template <int NQ>
 __device__ __forceinline__ void sum_partials(const double* __restrict__ part, int ntiles,
-                                             double (&out)[NQ]) {
-    __shared__ double red[kBlock][NQ];
+                                             double (&out)[NQ], double* scratch) {
+    double (*red)[NQ] = reinterpret_cast<double (*)[NQ]>(scratch);
     double s[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) s[q] = 0.0;
@@ -222,8 +319,8 @@ __device__ __forceinline__ void passA_rows(const ProbDesc& pd, int r_begin, int 
     T* __restrict__ LUb = static_cast<T*>(pd.LU);
     const T* __restrict__ LSb = static_cast<const T*>(pd.LS);
     uint8_t* __restrict__ choice = pd.choice;
-    const T c2 = T(2.0 * pd.inv_eps);
-    const T om = T(pd.omega0);
+    const T c2 = c2_of<T>(pd);
+    const T om = om_of<T>(pd);
     const T oma = sub_(T(1), alpha);
     const bool greedy = pd.oracle == 0;
     for (int r = r_begin + threadIdx.x; r < r_end; r += kBlock) {
@@ -274,6 +371,137 @@ __device__ __forceinline__ void passA_rows(const ProbDesc& pd, int r_begin, int 
         acc.tLU = add_(acc.tLU, tLU);
         acc.act = add_(acc.act, moved ? T(1) : T(0));
     }
+}
+
+// Staged pass A over rows [r_begin, r_end): for each 256-row sub-tile one
+// thread issues bulk copies of the sub-tile's class columns of U, LU (and LS
+// when a step is pending) into `stage` (T[3][KMAX][256]) on `bar`; then each
+// thread updates and evaluates its row from shared memory in two sweeps
+// (argmin, then the gap terms).  The arithmetic is the operation sequence of
+// passA_rows / row_eval, so results are bitwise the same.  Returns false when
+// a bulk-copy wait ran out of its bound (the copies are then waited for once
+// more before returning).
+template <typename T, int KMAX>
+__device__ __forceinline__ bool passA_staged(const ProbDesc& pd, int r_begin, int r_end, bool upd,
+                                             T alpha, AccA<T>& acc, T* stage, uint64_t* bar,
+                                             uint32_t& phase) {
+    const int K = pd.K;
+    const int64_t np = pd.npad;
+    T* __restrict__ Ub = static_cast<T*>(pd.U);
+    T* __restrict__ LUb = static_cast<T*>(pd.LU);
+    const T* __restrict__ LSb = static_cast<const T*>(pd.LS);
+    T* sU = stage;
+    T* sL = stage + KMAX * kBlock;
+    T* sS = stage + 2 * KMAX * kBlock;
+    const T c2 = c2_of<T>(pd);
+    const T om = om_of<T>(pd);
+    const T oma = sub_(T(1), alpha);
+    const bool greedy = pd.oracle == 0;
+    constexpr int kVec = 16 / int(sizeof(T));
+    bool ok = true;
+    for (int base = r_begin; base < r_end; base += kBlock) {
+        const int rows = min(kBlock, r_end - base);
+        // whole 16-byte units; the extra elements lie inside the npad-long columns
+        const uint32_t seg = uint32_t((rows + kVec - 1) / kVec * kVec) * uint32_t(sizeof(T));
+        if (threadIdx.x == 0) {
+            fence_proxy_async();
+            mbar_expect_tx(bar, seg * uint32_t(K) * (upd ? 3u : 2u));
+            for (int k = 0; k < K; ++k) {
+                bulk_g2s(sU + k * kBlock, Ub + k * np + base, seg, bar);
+                bulk_g2s(sL + k * kBlock, LUb + k * np + base, seg, bar);
+                if (upd) bulk_g2s(sS + k * kBlock, LSb + k * np + base, seg, bar);
+            }
+        }
+        if (!mbar_wait(bar, phase)) {
+            ok = false;
+            mbar_wait(bar, phase);
+        }
+        phase ^= 1u;
+        const int t = threadIdx.x;
+        if (t < rows) {
+            const int r = base + t;
+            int sp = 0;
+            bool mv = false;
+            if (upd) {
+                const uint8_t sv = ld_cg(pd.choice + r);
+                sp = sv & 0x7f;
+                mv = (sv & kActiveBit) != 0;
+            }
+            const int f = __ldg(pd.fid + r);
+            bool binary = true;
+            T best = inf_<T>();
+            int s = -1, first_adm = -1, first_one = -1;
+#pragma unroll
+            for (int k = 0; k < KMAX; ++k) {
+                if (k < K) {
+                    T u = sU[k * kBlock + t];
+                    T lu = sL[k * kBlock + t];
+                    if (upd) {
+                        lu = fma_(alpha, sS[k * kBlock + t], mul_(oma, lu));
+                        LUb[k * np + r] = lu;
+                        sL[k * kBlock + t] = lu;
+                        if (mv) {
+                            u = (k == sp) ? fma_(oma, u, alpha) : mul_(oma, u);
+                            Ub[k * np + r] = u;
+                            sU[k * kBlock + t] = u;
+                        }
+                    }
+                    binary = binary && (u == T(0) || u == T(1));
+                    if (first_one < 0 && u == T(1)) first_one = k;
+                    T gk = fma_(-c2, u, lu);
+                    if (f >= 0) gk = fma_(om, sub_(u, k == f ? T(1) : T(0)), gk);
+                    const bool adm = !greedy || u > T(0);
+                    if (adm && first_adm < 0) first_adm = k;
+                    if (adm && gk < best) {
+                        best = gk;
+                        s = k;
+                    }
+                }
+            }
+            const bool active = greedy ? !binary : true;
+            T gs = best;
+            if (active) {
+                if (s < 0) {   // no finite candidate: the gap becomes NaN
+                    s = first_adm < 0 ? 0 : first_adm;
+                    gs = CUDART_NAN_F;
+                }
+            } else {
+                s = first_one < 0 ? 0 : first_one;
+            }
+            const bool at_vertex = binary && sU[s * kBlock + t] == T(1);
+            const bool moved = active && !at_vertex;
+            if (moved) {
+                T gap = T(0), nD = T(0), tLU = T(0);
+#pragma unroll
+                for (int k = 0; k < KMAX; ++k) {
+                    if (k < K) {
+                        const T u = sU[k * kBlock + t];
+                        const T lu = sL[k * kBlock + t];
+                        T gk = fma_(-c2, u, lu);
+                        if (f >= 0) gk = fma_(om, sub_(u, k == f ? T(1) : T(0)), gk);
+                        const T d = sub_(k == s ? T(1) : T(0), u);
+                        gap = fma_(u, sub_(gk, gs), gap);
+                        nD = fma_(d, d, nD);
+                        tLU = fma_(d, lu, tLU);
+                    }
+                }
+                acc.g = add_(acc.g, gap);
+                acc.nD = add_(acc.nD, nD);
+                if (f >= 0) acc.nW = fma_(om, nD, acc.nW);
+                acc.tLU = add_(acc.tLU, tLU);
+                acc.act = add_(acc.act, T(1));
+            } else {
+                acc.g = add_(acc.g, T(0));
+                acc.nD = add_(acc.nD, T(0));
+                if (f >= 0) acc.nW = fma_(om, T(0), acc.nW);
+                acc.tLU = add_(acc.tLU, T(0));
+                acc.act = add_(acc.act, T(0));
+            }
+            pd.choice[r] = uint8_t(s) | (moved ? kActiveBit : uint8_t(0));
+        }
+        __syncthreads();
+    }
+    return ok;
 }
 
 // Stage 1 of the sparse passes: for each row of a 256-row sub-tile, `L` lanes
@@ -329,11 +557,11 @@ __device__ __forceinline__ void csr_bins(const ProbDesc& pd, const T* __restrict
                 int cc[8];
                 T v[8];
                 {
-                    const int4 c = __ldg(reinterpret_cast<const int4*>(col + e));
+                    const int4 c = ld_stream(reinterpret_cast<const int4*>(col + e));
                     cc[0] = c.x; cc[1] = c.y; cc[2] = c.z; cc[3] = c.w;
                 }
                 if (two) {
-                    const int4 c = __ldg(reinterpret_cast<const int4*>(col + e2));
+                    const int4 c = ld_stream(reinterpret_cast<const int4*>(col + e2));
                     cc[4] = c.x; cc[5] = c.y; cc[6] = c.z; cc[7] = c.w;
                 } else {
                     cc[4] = cc[5] = cc[6] = cc[7] = r;
@@ -477,7 +705,10 @@ __device__ __forceinline__ void finish_A(const ProbDesc& pd, ProbState* st,
     st->has_update = 0;
     int status = 2;  // FW_PENDING
     int done = 0;
-    if (!isfinite(S[0]) || !isfinite(S[1]) || !isfinite(S[2]) || !isfinite(S[3])) {
+    if (__ldcg(&st->err)) {
+        status = -7;  // FW_ERR_TIMEOUT
+        done = 1;
+    } else if (!isfinite(S[0]) || !isfinite(S[1]) || !isfinite(S[2]) || !isfinite(S[3])) {
         status = -6;  // FW_ERR_NUMERIC
         done = 1;
     } else if (st->active == 0 || S[0] <= 0.0) {
@@ -523,6 +754,7 @@ __device__ __forceinline__ void finish_B(const ProbDesc& pd, ProbState* st,
     st->pLS = S[0];
     st->q = q;
     st->alpha = a;
+    st->alpha_f = float(a);
     st->E = st->E - a * g + 0.5 * a * a * q;
     st->iter += 1;
     st->has_update = 1;
@@ -535,16 +767,19 @@ __device__ __forceinline__ void finish_B(const ProbDesc& pd, ProbState* st,
 // that stop in this pass.  Every thread of the block must call it.
 template <typename T, int KMAX>
 __device__ __forceinline__ void tile_A(const ProbDesc& pd, ProbState* st, int tile, bool upd,
-                                       T alpha, uint32_t* ndone) {
+                                       T alpha, uint32_t* ndone, T* stage, uint64_t* bar,
+                                       uint32_t& phase) {
     const int r0 = tile * pd.tile_rows;
     const int r1 = min(pd.n, r0 + pd.tile_rows);
     AccA<T> acc{T(0), T(0), T(0), T(0), T(0)};
-    passA_rows<T, KMAX, MODE_STEP>(pd, r0, r1, upd, alpha, acc, nullptr, nullptr);
+    if (!passA_staged<T, KMAX>(pd, r0, r1, upd, alpha, acc, stage, bar, phase) &&
+        threadIdx.x == 0)
+        atomicExch(&st->err, 1);
     const T v[kNumA] = {acc.g, acc.nD, acc.nW, acc.tLU, acc.act};
     block_partials<T, kNumA>(v, pd.partA + (size_t)tile * kNumA);
     if (last_to_arrive(&st->cntA, pd.ntiles)) {
         double S[kNumA];
-        sum_partials<kNumA>(pd.partA, pd.ntiles, S);
+        sum_partials<kNumA>(pd.partA, pd.ntiles, S, reinterpret_cast<double*>(stage));
         if (threadIdx.x == 0) {
             finish_A(pd, st, S);
             if (ndone && st->done) atomicAdd(ndone, 1u);
@@ -564,7 +799,7 @@ __device__ __forceinline__ void tile_B(const ProbDesc& pd, ProbState* st, int ti
     block_partials<T, kNumB>(v, pd.partB + (size_t)tile * kNumB);
     if (last_to_arrive(&st->cntB, pd.ntiles)) {
         double S[kNumB];
-        sum_partials<kNumB>(pd.partB, pd.ntiles, S);
+        sum_partials<kNumB>(pd.partB, pd.ntiles, S, reinterpret_cast<double*>(sm_lane));
         if (threadIdx.x == 0) {
             finish_B(pd, st, S);
             if (ndone && st->done) atomicAdd(ndone, 1u);

@@ -12,9 +12,15 @@ __global__ void __launch_bounds__(kBlock)
     k_passA(ProbDesc pd, ProbState* st, T* Gout, uint8_t* chout) {
     if (MODE != MODE_GRAD && ld_cg(&st->done)) return;
     const bool upd = ld_cg(&st->has_update) != 0;
-    const T alpha = T(ld_cg(&st->alpha));
-    if (MODE == MODE_STEP) {
-        tile_A<T, KMAX>(pd, st, blockIdx.x, upd, alpha, nullptr);
+    const T alpha = alpha_of<T>(st);
+    if constexpr (MODE == MODE_STEP) {
+        extern __shared__ __align__(128) unsigned char smraw[];
+        __shared__ __align__(8) uint64_t bar;
+        if (threadIdx.x == 0) mbar_init(&bar, 1);
+        __syncthreads();
+        uint32_t phase = 0;
+        tile_A<T, KMAX>(pd, st, blockIdx.x, upd, alpha, nullptr, reinterpret_cast<T*>(smraw), &bar,
+                        phase);
         return;
     }
     const int r0 = blockIdx.x * pd.tile_rows;
@@ -33,7 +39,7 @@ __global__ void __launch_bounds__(kBlock)
 template <typename T, typename WT, int KMAX>
 __global__ void __launch_bounds__(kBlock) k_passB(ProbDesc pd, ProbState* st) {
     if (ld_cg(&st->done)) return;
-    extern __shared__ __align__(16) unsigned char smraw[];
+    extern __shared__ __align__(128) unsigned char smraw[];
     T* sm_lane = reinterpret_cast<T*>(smraw);
     T* sm_row = sm_lane + kBlock * (KMAX | 1);
     tile_B<T, WT, KMAX, true>(pd, st, blockIdx.x, sm_lane, sm_row, nullptr);
@@ -42,7 +48,7 @@ __global__ void __launch_bounds__(kBlock) k_passB(ProbDesc pd, ProbState* st) {
 // OUT = L X (initial L U_0, refresh, direct objective).
 template <typename T, typename WT, int KMAX>
 __global__ void __launch_bounds__(kBlock) k_spmm(ProbDesc pd, const T* X, T* OUT) {
-    extern __shared__ __align__(16) unsigned char smraw[];
+    extern __shared__ __align__(128) unsigned char smraw[];
     T* sm_lane = reinterpret_cast<T*>(smraw);
     T* sm_row = sm_lane + kBlock * (KMAX | 1);
     const int r0 = blockIdx.x * pd.tile_rows;

@@ -12,17 +12,22 @@ public:
     size_t welem() const override { return sizeof(WT); }
     int kmax() const override { return KMAX; }
     static size_t smem() { return 2 * size_t(kBlock) * (KMAX | 1) * sizeof(T); }
+    static size_t smemA() { return 3 * size_t(kBlock) * KMAX * sizeof(T); }
     static unsigned rows_grid(const ProbDesc& pd) { return unsigned((pd.n + kBlock - 1) / kBlock); }
 
     cudaError_t configure() override {
-        cudaError_t e = cudaFuncSetAttribute(k_passB<T, WT, KMAX>,
+        cudaError_t e = cudaFuncSetAttribute(k_passA<T, KMAX, MODE_STEP>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             int(smemA()));
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(k_passB<T, WT, KMAX>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem()));
         if (e != cudaSuccess) return e;
         return cudaFuncSetAttribute(k_spmm<T, WT, KMAX>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem()));
     }
     void passA(const ProbDesc& pd, ProbState* st, cudaStream_t s) override {
-        k_passA<T, KMAX, MODE_STEP><<<pd.ntiles, kBlock, 0, s>>>(pd, st, nullptr, nullptr);
+        k_passA<T, KMAX, MODE_STEP><<<pd.ntiles, kBlock, smemA(), s>>>(pd, st, nullptr, nullptr);
     }
     void flush(const ProbDesc& pd, ProbState* st, cudaStream_t s) override {
         k_passA<T, KMAX, MODE_FLUSH><<<pd.ntiles, kBlock, 0, s>>>(pd, st, nullptr, nullptr);

@@ -55,8 +55,9 @@ __global__ void k_validate(int64_t n, const int32_t* rp, const int32_t* col, con
 }
 
 __global__ void __launch_bounds__(kBlock) k_state_init(ProbState* st, const double* part, int nb) {
+    __shared__ double red[kBlock];
     double S[1];
-    sum_partials<1>(part, nb, S);
+    sum_partials<1>(part, nb, S, red);
     if (threadIdx.x == 0) {
         ProbState z = {};
         z.status = 2;  // FW_PENDING
@@ -220,6 +221,9 @@ void place_problem(char* base, const ProbLayout& lay, size_t te, size_t we, cons
     pd.inv_eps = std::isinf(o.eps) ? 0.0 : 1.0 / o.eps;
     pd.omega0 = o.omega0;
     pd.gap_tol = o.gap_tol;
+    pd.c2 = 2.0 * pd.inv_eps;
+    pd.c2f = float(pd.c2);
+    pd.omf = float(pd.omega0);
 }
 
 #define FW_TRYS(x)                      \

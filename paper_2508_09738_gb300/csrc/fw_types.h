@@ -43,12 +43,17 @@ struct ProbDesc {
     double inv_eps;      // 1/eps (0 when eps = +inf)
     double omega0;       // fidelity weight
     double gap_tol;
+    double c2;           // 2/eps rounded to the iterate type by the kernels
+    float c2f;           // 2/eps as float (FP32 iterate)
+    float omf;           // omega0 as float
 };
 
 // Mutable per-problem state, in device memory.  Written only by the last
 // block to finish a pass of the problem, read by all blocks of the next pass.
 struct ProbState {
     double g, g0, nD, nW, tLU, pLS, q, alpha, E;
+    float alpha_f;       // alpha rounded to float, for the FP32 update
+    int32_t err;         // set by any block whose bulk-copy wait ran out
     int32_t iter;        // updates applied
     int32_t status;      // fw_status once done, FW_PENDING (2) while running
     int32_t active;      // |I_k|
