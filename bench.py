@@ -477,7 +477,7 @@ def main():
 
     # per-pass device times (CUDA events on the solver's stream) -> roofline
     seg.reset()
-    ms_a, ms_b = seg.profile(min(args.profile_iters, iters))
+    ms_a, ms_b, ms_f = seg.profile(min(args.profile_iters, iters))
     wb = {"f32": 4, "bf16": 2, "f64": 8}[weights]
     tb = 8 if weights == "f64" else 4
     by = bytes_per_unit(g.n, g.nnz, g.K, wb, tb)
@@ -491,7 +491,7 @@ def main():
                 "traffic": ncu_traffic(kernel_name, args.workload),
                 "kernel": kernel_name, "peak_source": peaks["source"],
                 "algorithmic_bytes_per_launch": by[dom],
-                "kernel_ms": {"k_passA": ms_a, "k_passB": ms_b}}
+                "kernel_ms": {"k_passA": ms_a, "k_passB": ms_b, "k_finish": ms_f}}
     seg.close()
 
     # end to end through the C ABI from pinned host buffers

@@ -161,10 +161,12 @@ fw_status fw_seg_refresh(fw_seg *h);
 fw_status fw_seg_reset(fw_seg *h);
 
 /* Measurement: run `iters` iterations as separate launches with CUDA events
- * around each pass on the handle's stream; *ms_row_pass and *ms_csr_pass get
- * the mean device time of pass A (update, gradient, GLMO, gap) and pass B
- * (one-hot L S, line search) in milliseconds.  The iterate advances. */
-fw_status fw_seg_profile(fw_seg *h, int32_t iters, double *ms_row_pass, double *ms_csr_pass);
+ * around each kernel on the handle's stream; the outputs (each nullable) get
+ * the mean device time in milliseconds of pass A (update, gradient, GLMO, gap
+ * pieces), pass B (one-hot L S, <D, L S>) and the finishing kernel (reduction
+ * of both passes' tile records, stop test, line search).  The iterate advances. */
+fw_status fw_seg_profile(fw_seg *h, int32_t iters, double *ms_row_pass, double *ms_csr_pass,
+                         double *ms_finish);
 
 /* Statistics of the handle's current state. */
 fw_status fw_seg_get_stats(fw_seg *h, fw_seg_stats *stats);

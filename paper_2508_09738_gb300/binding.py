@@ -110,7 +110,8 @@ _SIGS = {
     "fw_seg_refresh": (c_int32, [c_void_p]),
     "fw_seg_get_stats": (c_int32, [c_void_p, POINTER(fw_seg_stats)]),
     "fw_seg_reset": (c_int32, [c_void_p]),
-    "fw_seg_profile": (c_int32, [c_void_p, c_int32, POINTER(c_double), POINTER(c_double)]),
+    "fw_seg_profile": (c_int32, [c_void_p, c_int32, POINTER(c_double), POINTER(c_double),
+                                 POINTER(c_double)]),
     "fw_seg_destroy": (None, [c_void_p]),
     "fw_batch_default_opts": (c_int32, [POINTER(fw_batch_opts)]),
     "fw_batch_create": (c_int32, [POINTER(c_void_p), c_int32, POINTER(fw_graph),
@@ -272,10 +273,11 @@ def fw_seg_reset(h: Handle) -> None:
 
 
 def fw_seg_profile(h: Handle, iters: int):
-    """Mean device ms of (pass A, pass B) over `iters` separately launched iterations."""
-    a, b = c_double(), c_double()
-    _check(lib().fw_seg_profile(h.ptr, int(iters), ctypes.byref(a), ctypes.byref(b)))
-    return a.value, b.value
+    """Mean device ms of (pass A, pass B, finish) over `iters` separately launched iterations."""
+    a, b, f = c_double(), c_double(), c_double()
+    _check(lib().fw_seg_profile(h.ptr, int(iters), ctypes.byref(a), ctypes.byref(b),
+                                ctypes.byref(f)))
+    return a.value, b.value, f.value
 
 
 def fw_seg_destroy(h: Handle) -> None:

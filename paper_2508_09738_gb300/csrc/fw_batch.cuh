@@ -83,10 +83,13 @@ __global__ void __launch_bounds__(kBlock) k_persistent(BatchArgs a) {
     __shared__ ProbDesc s_pd;
     __shared__ int s_w, s_skip, s_upd;
     __shared__ T s_alpha;
-    __shared__ __align__(8) uint64_t bar;
-    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __shared__ __align__(8) uint64_t bars[2];
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+    }
     __syncthreads();
-    uint32_t mb_phase = 0;   // parity of the bulk-copy mbarrier
+    uint32_t mb_phases = 0;   // parities of the two bulk-copy mbarriers
     for (int it = 0; it < a.iters; ++it) {
         for (int phase = 0; phase < 2; ++phase) {
             int w = blockIdx.x;
@@ -110,11 +113,12 @@ __global__ void __launch_bounds__(kBlock) k_persistent(BatchArgs a) {
                     const int2 wk = a.work[ww];
                     ProbState* st = a.state + wk.x;
                     if (phase == 0)
-                        tile_A<T, KMAX>(s_pd, st, wk.y, s_upd != 0, s_alpha, &a.bar->ndone, stage,
-                                        &bar, mb_phase);
+                        tile_A<T, KMAX>(s_pd, st, wk.y, s_upd != 0, s_alpha, stage,
+                                        s_pd.tile_rows > kBlock ? max_stages<T, KMAX>() : 1,
+                                        bars, mb_phases);
                     else
-                        tile_B<T, WT, KMAX, false>(s_pd, st, wk.y, sm_lane, sm_row,
-                                                   &a.bar->ndone);
+                        tile_B<T, WT, KMAX, false, true>(s_pd, st, wk.y, sm_lane, sm_row,
+                                                         &a.bar->ndone);
                 }
                 __syncthreads();
                 w += gridDim.x;
@@ -143,8 +147,10 @@ class BatchKernImpl final : public BatchKern {
 public:
     size_t smem() const override {
         const size_t b = 2 * size_t(kBlock) * (KMAX | 1) * sizeof(T);
-        const size_t a = 3 * size_t(kBlock) * KMAX * sizeof(T);
-        return a > b ? a : b;
+        const size_t a = max_stages<T, KMAX>() * 3 * size_t(kBlock) * KMAX * sizeof(T);
+        const size_t r = size_t(kBlock) * kNumR * sizeof(double);
+        const size_t m = a > b ? a : b;
+        return m > r ? m : r;
     }
     cudaError_t configure() override {
         return cudaFuncSetAttribute(k_persistent<T, WT, KMAX>,

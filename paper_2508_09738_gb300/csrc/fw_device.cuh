@@ -159,26 +159,30 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // ------------------------------------------------------- block reductions
-// Sum NQ per-thread values over the block: FP32 (or FP64) butterfly inside each
-// warp, FP64 across the warps in a fixed order.  Thread q < NQ writes out[q].
+// GB300 executes FP64 at a small fraction of the FP32 rate, so FP64 is used
+// only where sums span many tiles: rows of one 256-row tile are summed in the
+// iterate type T (warp butterfly, then the 8 warps in a fixed order) and the
+// tile total is widened to double once per quantity.
+
+// Sum NQ per-thread values over the block; thread q < NQ writes out[q].
 // Must be reached by every thread of the block.
 template <typename T, int NQ>
 __device__ __forceinline__ void block_partials(const T (&v)[NQ], double* __restrict__ out) {
-    __shared__ double red[kBlock / 32][NQ];
+    __shared__ T red[kBlock / 32][NQ];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
         T x = v[q];
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) x = add_(x, __shfl_xor_sync(0xffffffffu, x, off));
-        if (lane == 0) red[warp][q] = double(x);
+        if (lane == 0) red[warp][q] = x;
     }
     __syncthreads();
     if (threadIdx.x < NQ) {
-        double s = 0.0;
+        T s = T(0);
 #pragma unroll
         for (int w = 0; w < kBlock / 32; ++w) s = add_(s, red[w][threadIdx.x]);
-        out[threadIdx.x] = s;
+        out[threadIdx.x] = double(s);
     }
     __syncthreads();
 }
@@ -198,33 +202,107 @@ __device__ __forceinline__ bool last_to_arrive(uint32_t* cnt, uint32_t total) {
     return last;
 }
 
-// Fixed-order FP64 sum of ntiles partial records of NQ doubles (L2 loads).
+// ------------------------------------------ exact order-free accumulation
+// A finite double v with |v| < 2^62 is added to a 128-bit two's-complement
+// fixed-point number with 64 fraction bits (lo, hi words): v = hi + frac with
+// hi = floor(v), frac in [0, 1) exactly, and frac * 2^64 truncated to an
+// integer (parts below 2^-64 are dropped).  The carry of the low-word add is
+// exact, so the total is the exact sum of the added values whatever the order
+// of the atomic operations.  Non-finite values raise the flag word instead.
+__device__ __forceinline__ void fx_add(unsigned long long* acc, int q, double v) {
+    if (!isfinite(v) || fabs(v) >= 4.0e18) {
+        atomicOr(&acc[2 * kNumR], 1ull);
+        return;
+    }
+    const double fl = floor(v);
+    const unsigned long long lo = __double2ull_rz(ldexp(v - fl, 64));
+    const unsigned long long hi = static_cast<unsigned long long>(__double2ll_rz(fl));
+    const unsigned long long old = atomicAdd(&acc[2 * q], lo);
+    const unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
+    atomicAdd(&acc[2 * q + 1], hi + carry);
+}
+
+__device__ __forceinline__ double fx_get(const unsigned long long* acc, int q) {
+    const long long hi = static_cast<long long>(__ldcg(&acc[2 * q + 1]));
+    const unsigned long long lo = __ldcg(&acc[2 * q]);
+    return double(hi) + ldexp(double(lo), -64);
+}
+
+// Sum NQ per-thread values over the block (as block_partials) and add the
+// block total to the fixed-point accumulators acc[q0 .. q0+NQ).
+template <typename T, int NQ>
+__device__ __forceinline__ void block_accumulate(const T (&v)[NQ], unsigned long long* acc, int q0) {
+    __shared__ T red[kBlock / 32][NQ];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        T x = v[q];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) x = add_(x, __shfl_xor_sync(0xffffffffu, x, off));
+        if (lane == 0) red[warp][q] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < NQ) {
+        T s = T(0);
+#pragma unroll
+        for (int w = 0; w < kBlock / 32; ++w) s = add_(s, red[w][threadIdx.x]);
+        fx_add(acc, q0 + threadIdx.x, double(s));
+    }
+    __syncthreads();
+}
+
+// Fixed-order FP64 sum of `count` records of NQ doubles: thread t loads
+// records t, t+kBlock, ... (four records ahead, so up to 4*kBlock records take
+// one round trip) and adds them in that order; warp 0 then adds the threads'
+// sums (lane l: threads l, l+32, ..., in order) and a butterfly finishes.
 // `scratch` is kBlock*NQ doubles of shared memory.  Every thread of the block
 // must call it; out[] is valid in all threads.
 template <int NQ>
-__device__ __forceinline__ void sum_partials(const double* __restrict__ part, int ntiles,
+__device__ __forceinline__ void sum_partials(const double* __restrict__ part, int count,
                                              double (&out)[NQ], double* scratch) {
-    double (*red)[NQ] = reinterpret_cast<double (*)[NQ]>(scratch);
+    constexpr int kAhead = 4;
     double s[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) s[q] = 0.0;
-    for (int t = threadIdx.x; t < ntiles; t += kBlock) {
+    for (int t0 = threadIdx.x; t0 < count; t0 += kAhead * kBlock) {
+        double v[kAhead][NQ];
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) s[q] = add_(s[q], __ldcg(part + (size_t)t * NQ + q));
-    }
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) red[threadIdx.x][q] = s[q];
-    __syncthreads();
-    for (int stride = kBlock / 2; stride > 0; stride >>= 1) {
-        if (threadIdx.x < stride) {
+        for (int a = 0; a < kAhead; ++a) {
+            const int t = t0 + a * kBlock;
 #pragma unroll
             for (int q = 0; q < NQ; ++q)
-                red[threadIdx.x][q] = add_(red[threadIdx.x][q], red[threadIdx.x + stride][q]);
+                v[a][q] = t < count ? __ldcg(part + (size_t)t * NQ + q) : 0.0;
         }
-        __syncthreads();
+#pragma unroll
+        for (int a = 0; a < kAhead; ++a)
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) s[q] = add_(s[q], v[a][q]);
     }
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) out[q] = red[0][q];
+    for (int q = 0; q < NQ; ++q) scratch[threadIdx.x * NQ + q] = s[q];
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double w[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) w[q] = 0.0;
+#pragma unroll
+        for (int i = 0; i < kBlock / 32; ++i)
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) w[q] = add_(w[q], scratch[(threadIdx.x + 32 * i) * NQ + q]);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1)
+                w[q] = add_(w[q], __shfl_xor_sync(0xffffffffu, w[q], off));
+        }
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) scratch[q] = w[q];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) out[q] = scratch[q];
     __syncthreads();
 }
 
@@ -373,61 +451,84 @@ __device__ __forceinline__ void passA_rows(const ProbDesc& pd, int r_begin, int 
     }
 }
 
-// Staged pass A over rows [r_begin, r_end): for each 256-row sub-tile one
-// thread issues bulk copies of the sub-tile's class columns of U, LU (and LS
-// when a step is pending) into `stage` (T[3][KMAX][256]) on `bar`; then each
-// thread updates and evaluates its row from shared memory in two sweeps
-// (argmin, then the gap terms).  The arithmetic is the operation sequence of
-// passA_rows / row_eval, so results are bitwise the same.  Returns false when
-// a bulk-copy wait ran out of its bound (the copies are then waited for once
-// more before returning).
+// Staged pass A over rows [r_begin, r_end) in 256-row sub-tiles.  For each
+// sub-tile one thread issues bulk copies of its class columns of U, LU (and LS
+// when a step is pending) into a stage buffer (T[3][KMAX][256]) completing on
+// that buffer's mbarrier; with two stages the copies of sub-tile j+1 are in
+// flight while sub-tile j is computed.  Each thread updates and evaluates its
+// row from shared memory in two sweeps (argmin, then the gap terms), with the
+// operation sequence of passA_rows / row_eval, so results are bitwise the
+// same.  Returns false when a copy wait ran out of its bound (the copies are
+// then waited for once more).
+// Stages of the pass-A staging buffer that fit next to the rest (2 unless one
+// stage is larger than 100 KB, e.g. FP64 with K > 16).
+template <typename T, int KMAX>
+__host__ __device__ constexpr int max_stages() {
+    return 2 * 3 * kBlock * KMAX * int(sizeof(T)) <= 200 * 1024 ? 2 : 1;
+}
+
+template <typename T, int KMAX>
+__device__ __forceinline__ void stage_issue(const ProbDesc& pd, int base, int rows, bool upd,
+                                            T* stage, uint64_t* bar) {
+    constexpr int kVec = 16 / int(sizeof(T));
+    const int K = pd.K;
+    const int64_t np = pd.npad;
+    // whole 16-byte units; the extra elements lie inside the npad-long columns
+    const uint32_t seg = uint32_t((rows + kVec - 1) / kVec * kVec) * uint32_t(sizeof(T));
+    fence_proxy_async();
+    mbar_expect_tx(bar, seg * uint32_t(K) * (upd ? 3u : 2u));
+    const T* Ub = static_cast<const T*>(pd.U);
+    const T* LUb = static_cast<const T*>(pd.LU);
+    const T* LSb = static_cast<const T*>(pd.LS);
+    for (int k = 0; k < K; ++k) {
+        bulk_g2s(stage + k * kBlock, Ub + k * np + base, seg, bar);
+        bulk_g2s(stage + (KMAX + k) * kBlock, LUb + k * np + base, seg, bar);
+        if (upd) bulk_g2s(stage + (2 * KMAX + k) * kBlock, LSb + k * np + base, seg, bar);
+    }
+}
+
 template <typename T, int KMAX>
 __device__ __forceinline__ bool passA_staged(const ProbDesc& pd, int r_begin, int r_end, bool upd,
-                                             T alpha, AccA<T>& acc, T* stage, uint64_t* bar,
-                                             uint32_t& phase) {
+                                             T alpha, AccA<T>& acc, T* stage, int nstages,
+                                             uint64_t* bars, uint32_t& phases) {
     const int K = pd.K;
     const int64_t np = pd.npad;
     T* __restrict__ Ub = static_cast<T*>(pd.U);
     T* __restrict__ LUb = static_cast<T*>(pd.LU);
-    const T* __restrict__ LSb = static_cast<const T*>(pd.LS);
-    T* sU = stage;
-    T* sL = stage + KMAX * kBlock;
-    T* sS = stage + 2 * KMAX * kBlock;
     const T c2 = c2_of<T>(pd);
     const T om = om_of<T>(pd);
     const T oma = sub_(T(1), alpha);
     const bool greedy = pd.oracle == 0;
-    constexpr int kVec = 16 / int(sizeof(T));
+    const int stage_elems = 3 * KMAX * kBlock;
     bool ok = true;
-    for (int base = r_begin; base < r_end; base += kBlock) {
+    if (threadIdx.x == 0 && r_begin < r_end)
+        stage_issue<T, KMAX>(pd, r_begin, min(kBlock, r_end - r_begin), upd, stage, &bars[0]);
+    int j = 0;
+    for (int base = r_begin; base < r_end; base += kBlock, ++j) {
+        const int buf = nstages > 1 ? (j & 1) : 0;
         const int rows = min(kBlock, r_end - base);
-        // whole 16-byte units; the extra elements lie inside the npad-long columns
-        const uint32_t seg = uint32_t((rows + kVec - 1) / kVec * kVec) * uint32_t(sizeof(T));
-        if (threadIdx.x == 0) {
-            fence_proxy_async();
-            mbar_expect_tx(bar, seg * uint32_t(K) * (upd ? 3u : 2u));
-            for (int k = 0; k < K; ++k) {
-                bulk_g2s(sU + k * kBlock, Ub + k * np + base, seg, bar);
-                bulk_g2s(sL + k * kBlock, LUb + k * np + base, seg, bar);
-                if (upd) bulk_g2s(sS + k * kBlock, LSb + k * np + base, seg, bar);
-            }
-        }
-        if (!mbar_wait(bar, phase)) {
-            ok = false;
-            mbar_wait(bar, phase);
-        }
-        phase ^= 1u;
+        T* sU = stage + buf * stage_elems;
+        T* sL = sU + KMAX * kBlock;
+        T* sS = sU + 2 * KMAX * kBlock;
         const int t = threadIdx.x;
+        const int r = base + t;
+        // per-row bytes are loaded before the wait so their latency overlaps the copies
+        const uint8_t sv = (t < rows && upd) ? ld_cg(pd.choice + r) : uint8_t(0);
+        const int f = t < rows ? int(__ldg(pd.fid + r)) : -1;
+        if (nstages > 1 && threadIdx.x == 0 && base + kBlock < r_end) {
+            const int nb = base + kBlock;   // prefetch the next sub-tile into the other buffer
+            stage_issue<T, KMAX>(pd, nb, min(kBlock, r_end - nb), upd,
+                                 stage + (buf ^ 1) * stage_elems, &bars[buf ^ 1]);
+        }
+        const uint32_t par = (phases >> buf) & 1u;
+        if (!mbar_wait(&bars[buf], par)) {
+            ok = false;
+            mbar_wait(&bars[buf], par);
+        }
+        phases ^= 1u << buf;
         if (t < rows) {
-            const int r = base + t;
-            int sp = 0;
-            bool mv = false;
-            if (upd) {
-                const uint8_t sv = ld_cg(pd.choice + r);
-                sp = sv & 0x7f;
-                mv = (sv & kActiveBit) != 0;
-            }
-            const int f = __ldg(pd.fid + r);
+            const int sp = sv & 0x7f;
+            const bool mv = (sv & kActiveBit) != 0;
             bool binary = true;
             T best = inf_<T>();
             int s = -1, first_adm = -1, first_one = -1;
@@ -470,8 +571,8 @@ __device__ __forceinline__ bool passA_staged(const ProbDesc& pd, int r_begin, in
             }
             const bool at_vertex = binary && sU[s * kBlock + t] == T(1);
             const bool moved = active && !at_vertex;
+            T gap = T(0), nD = T(0), tLU = T(0);
             if (moved) {
-                T gap = T(0), nD = T(0), tLU = T(0);
 #pragma unroll
                 for (int k = 0; k < KMAX; ++k) {
                     if (k < K) {
@@ -485,18 +586,12 @@ __device__ __forceinline__ bool passA_staged(const ProbDesc& pd, int r_begin, in
                         tLU = fma_(d, lu, tLU);
                     }
                 }
-                acc.g = add_(acc.g, gap);
-                acc.nD = add_(acc.nD, nD);
-                if (f >= 0) acc.nW = fma_(om, nD, acc.nW);
-                acc.tLU = add_(acc.tLU, tLU);
-                acc.act = add_(acc.act, T(1));
-            } else {
-                acc.g = add_(acc.g, T(0));
-                acc.nD = add_(acc.nD, T(0));
-                if (f >= 0) acc.nW = fma_(om, T(0), acc.nW);
-                acc.tLU = add_(acc.tLU, T(0));
-                acc.act = add_(acc.act, T(0));
             }
+            acc.g = add_(acc.g, gap);
+            acc.nD = add_(acc.nD, nD);
+            if (f >= 0) acc.nW = fma_(om, nD, acc.nW);
+            acc.tLU = add_(acc.tLU, tLU);
+            acc.act = add_(acc.act, moved ? T(1) : T(0));
             pd.choice[r] = uint8_t(s) | (moved ? kActiveBit : uint8_t(0));
         }
         __syncthreads();
@@ -690,14 +785,17 @@ __device__ __forceinline__ void spmm_rows(const ProbDesc& pd, const T* __restric
 }
 
 // ------------------------------------------------------------ scalar steps
-// Run by one thread of the last block of pass A: stop test of Alg. 3 step 4.
-__device__ __forceinline__ void finish_A(const ProbDesc& pd, ProbState* st,
-                                         const double (&S)[kNumA]) {
+// Run by one thread of the last block of pass B with the problem totals
+// S = (g, ||D||^2, sum w||D||^2, <D,LU>, |I|, <D,LS>) of this iteration:
+// the stop test of Alg. 3 step 4, then the curvature and the step.
+__device__ __forceinline__ void finish_iter(const ProbDesc& pd, ProbState* st,
+                                            const double (&S)[kNumR]) {
     st->g = S[0];
     st->nD = S[1];
     st->nW = S[2];
     st->tLU = S[3];
     st->active = int(S[4]);
+    st->pLS = S[5];
     if (!st->g0_set) {
         st->g0 = S[0];
         st->g0_set = 1;
@@ -708,7 +806,8 @@ __device__ __forceinline__ void finish_A(const ProbDesc& pd, ProbState* st,
     if (__ldcg(&st->err)) {
         status = -7;  // FW_ERR_TIMEOUT
         done = 1;
-    } else if (!isfinite(S[0]) || !isfinite(S[1]) || !isfinite(S[2]) || !isfinite(S[3])) {
+    } else if (!isfinite(S[0]) || !isfinite(S[1]) || !isfinite(S[2]) || !isfinite(S[3]) ||
+               !isfinite(S[5])) {
         status = -6;  // FW_ERR_NUMERIC
         done = 1;
     } else if (st->active == 0 || S[0] <= 0.0) {
@@ -726,22 +825,16 @@ __device__ __forceinline__ void finish_A(const ProbDesc& pd, ProbState* st,
     }
     st->status = status;
     st->done = done;
-    st->cntA = 0;
-}
-
-// Run by one thread of the last block of pass B: curvature and step.
-__device__ __forceinline__ void finish_B(const ProbDesc& pd, ProbState* st,
-                                         const double (&S)[kNumB]) {
-    const double qL = S[0] - st->tLU;                       // <D, L D>
-    const double q = qL + st->nW - 2.0 * pd.inv_eps * st->nD;  // <D, H D>
-    const double g = st->g;
-    double a = 1.0;
+    if (done) return;
+    const double g = S[0];
+    const double qL = S[5] - S[3];                        // <D, L D>
+    const double q = qL + S[2] - 2.0 * pd.inv_eps * S[1];  // <D, H D>
     if (!isfinite(q)) {
         st->status = -6;
         st->done = 1;
-        st->cntB = 0;
         return;
     }
+    double a = 1.0;
     if (pd.step_rule == 0) {
         if (q > 0.0) a = fmin(1.0, g / q);
     } else {
@@ -751,14 +844,24 @@ __device__ __forceinline__ void finish_B(const ProbDesc& pd, ProbState* st,
             for (int j = 0; j < 1100 && a > amax; ++j) a *= 0.5;
         }
     }
-    st->pLS = S[0];
     st->q = q;
     st->alpha = a;
     st->alpha_f = float(a);
     st->E = st->E - a * g + 0.5 * a * a * q;
     st->iter += 1;
     st->has_update = 1;
-    st->cntB = 0;
+}
+
+// Read this iteration's totals from the accumulators, clear them, and run
+// finish_iter (one thread).
+__device__ __forceinline__ void finish_from_acc(const ProbDesc& pd, ProbState* st) {
+    double S[kNumR];
+#pragma unroll
+    for (int q = 0; q < kNumR; ++q) S[q] = fx_get(pd.acc, q);
+    if (__ldcg(&pd.acc[2 * kNumR])) S[0] = CUDART_NAN;
+#pragma unroll
+    for (int q = 0; q < 2 * kNumR + 1; ++q) pd.acc[q] = 0ull;
+    finish_iter(pd, st, S);
 }
 
 // ------------------------------------------------------------- row tiles
@@ -767,28 +870,23 @@ __device__ __forceinline__ void finish_B(const ProbDesc& pd, ProbState* st,
 // that stop in this pass.  Every thread of the block must call it.
 template <typename T, int KMAX>
 __device__ __forceinline__ void tile_A(const ProbDesc& pd, ProbState* st, int tile, bool upd,
-                                       T alpha, uint32_t* ndone, T* stage, uint64_t* bar,
-                                       uint32_t& phase) {
+                                       T alpha, T* stage, int nstages, uint64_t* bars,
+                                       uint32_t& phases) {
     const int r0 = tile * pd.tile_rows;
     const int r1 = min(pd.n, r0 + pd.tile_rows);
     AccA<T> acc{T(0), T(0), T(0), T(0), T(0)};
-    if (!passA_staged<T, KMAX>(pd, r0, r1, upd, alpha, acc, stage, bar, phase) &&
+    if (!passA_staged<T, KMAX>(pd, r0, r1, upd, alpha, acc, stage, nstages, bars, phases) &&
         threadIdx.x == 0)
         atomicExch(&st->err, 1);
     const T v[kNumA] = {acc.g, acc.nD, acc.nW, acc.tLU, acc.act};
-    block_partials<T, kNumA>(v, pd.partA + (size_t)tile * kNumA);
-    if (last_to_arrive(&st->cntA, pd.ntiles)) {
-        double S[kNumA];
-        sum_partials<kNumA>(pd.partA, pd.ntiles, S, reinterpret_cast<double*>(stage));
-        if (threadIdx.x == 0) {
-            finish_A(pd, st, S);
-            if (ndone && st->done) atomicAdd(ndone, 1u);
-        }
-    }
+    block_accumulate<T, kNumA>(v, pd.acc, 0);
 }
 
-// One row tile of pass B; the last tile of the problem forms q and the step.
-template <typename T, typename WT, int KMAX, bool RO>
+// One row tile of pass B.  With LAST, the last tile of the problem to finish
+// runs finish_iter on the accumulated totals (persistent kernel); otherwise a
+// separate k_finish launch does that.  `ndone` (nullable) counts problems
+// that stop.
+template <typename T, typename WT, int KMAX, bool RO, bool LAST>
 __device__ __forceinline__ void tile_B(const ProbDesc& pd, ProbState* st, int tile, T* sm_lane,
                                        T* sm_row, uint32_t* ndone) {
     const int r0 = tile * pd.tile_rows;
@@ -796,14 +894,11 @@ __device__ __forceinline__ void tile_B(const ProbDesc& pd, ProbState* st, int ti
     T accq = T(0);
     passB_rows<T, WT, KMAX, RO>(pd, r0, r1, accq, sm_lane, sm_row);
     const T v[kNumB] = {accq};
-    block_partials<T, kNumB>(v, pd.partB + (size_t)tile * kNumB);
-    if (last_to_arrive(&st->cntB, pd.ntiles)) {
-        double S[kNumB];
-        sum_partials<kNumB>(pd.partB, pd.ntiles, S, reinterpret_cast<double*>(sm_lane));
-        if (threadIdx.x == 0) {
-            finish_B(pd, st, S);
-            if (ndone && st->done) atomicAdd(ndone, 1u);
-        }
+    block_accumulate<T, kNumB>(v, pd.acc, kNumA);
+    if (LAST && last_to_arrive(&st->cnt, pd.ntiles) && threadIdx.x == 0) {
+        st->cnt = 0;
+        finish_from_acc(pd, st);
+        if (ndone && st->done) atomicAdd(ndone, 1u);
     }
 }
 

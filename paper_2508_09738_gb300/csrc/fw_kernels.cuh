@@ -15,12 +15,16 @@ __global__ void __launch_bounds__(kBlock)
     const T alpha = alpha_of<T>(st);
     if constexpr (MODE == MODE_STEP) {
         extern __shared__ __align__(128) unsigned char smraw[];
-        __shared__ __align__(8) uint64_t bar;
-        if (threadIdx.x == 0) mbar_init(&bar, 1);
+        __shared__ __align__(8) uint64_t bars[2];
+        if (threadIdx.x == 0) {
+            mbar_init(&bars[0], 1);
+            mbar_init(&bars[1], 1);
+        }
         __syncthreads();
-        uint32_t phase = 0;
-        tile_A<T, KMAX>(pd, st, blockIdx.x, upd, alpha, nullptr, reinterpret_cast<T*>(smraw), &bar,
-                        phase);
+        uint32_t phases = 0;
+        const int nst = (pd.tile_rows > kBlock && max_stages<T, KMAX>() == 2) ? 2 : 1;
+        tile_A<T, KMAX>(pd, st, blockIdx.x, upd, alpha, reinterpret_cast<T*>(smraw), nst, bars,
+                        phases);
         return;
     }
     const int r0 = blockIdx.x * pd.tile_rows;
@@ -42,7 +46,13 @@ __global__ void __launch_bounds__(kBlock) k_passB(ProbDesc pd, ProbState* st) {
     extern __shared__ __align__(128) unsigned char smraw[];
     T* sm_lane = reinterpret_cast<T*>(smraw);
     T* sm_row = sm_lane + kBlock * (KMAX | 1);
-    tile_B<T, WT, KMAX, true>(pd, st, blockIdx.x, sm_lane, sm_row, nullptr);
+    tile_B<T, WT, KMAX, true, false>(pd, st, blockIdx.x, sm_lane, sm_row, nullptr);
+}
+
+// One thread after pass B: read the iteration's totals (complete after the
+// kernel boundary), run the stop test and the step.
+static __global__ void k_finish(ProbDesc pd, ProbState* st) {
+    if (threadIdx.x == 0 && !ld_cg(&st->done)) finish_from_acc(pd, st);
 }
 
 // OUT = L X (initial L U_0, refresh, direct objective).

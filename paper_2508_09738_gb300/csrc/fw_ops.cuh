@@ -11,8 +11,13 @@ public:
     size_t elem() const override { return sizeof(T); }
     size_t welem() const override { return sizeof(WT); }
     int kmax() const override { return KMAX; }
+    // pass B / SpMM bins
     static size_t smem() { return 2 * size_t(kBlock) * (KMAX | 1) * sizeof(T); }
-    static size_t smemA() { return 3 * size_t(kBlock) * KMAX * sizeof(T); }
+    static size_t smemA() { return max_stages<T, KMAX>() * 3 * size_t(kBlock) * KMAX * sizeof(T); }
+    static size_t smemA(const ProbDesc& pd) {
+        return (pd.tile_rows > kBlock ? max_stages<T, KMAX>() : 1) * 3 * size_t(kBlock) * KMAX *
+               sizeof(T);
+    }
     static unsigned rows_grid(const ProbDesc& pd) { return unsigned((pd.n + kBlock - 1) / kBlock); }
 
     cudaError_t configure() override {
@@ -27,7 +32,7 @@ public:
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem()));
     }
     void passA(const ProbDesc& pd, ProbState* st, cudaStream_t s) override {
-        k_passA<T, KMAX, MODE_STEP><<<pd.ntiles, kBlock, smemA(), s>>>(pd, st, nullptr, nullptr);
+        k_passA<T, KMAX, MODE_STEP><<<pd.ntiles, kBlock, smemA(pd), s>>>(pd, st, nullptr, nullptr);
     }
     void flush(const ProbDesc& pd, ProbState* st, cudaStream_t s) override {
         k_passA<T, KMAX, MODE_FLUSH><<<pd.ntiles, kBlock, 0, s>>>(pd, st, nullptr, nullptr);
@@ -38,6 +43,9 @@ public:
     }
     void passB(const ProbDesc& pd, ProbState* st, cudaStream_t s) override {
         k_passB<T, WT, KMAX><<<pd.ntiles, kBlock, smem(), s>>>(pd, st);
+    }
+    void finish(const ProbDesc& pd, ProbState* st, cudaStream_t s) override {
+        k_finish<<<1, 32, 0, s>>>(pd, st);
     }
     void spmm(const ProbDesc& pd, const void* X, void* out, cudaStream_t s) override {
         k_spmm<T, WT, KMAX><<<pd.ntiles, kBlock, smem(), s>>>(pd, (const T*)X, (T*)out);

@@ -3,7 +3,9 @@
 // Device state of a handle (one GPU, resident for the handle's lifetime, one
 // allocation): padded CSR of the off-diagonal operator (int32 row_ptr / col,
 // WT weights), U, L U, L S in class-major layout (T[K][npad]), choice (uint8)
-// and fid (int8) per row, per-tile FP64 partials, and one ProbState.
+// and fid (int8) per row, per-tile FP64 partial records, and one ProbState.
+// Pass A writes its per-tile records only; the last block of pass B reduces
+// the records of both passes, runs the stop test and computes the step.
 // A solve launches a CUDA graph that holds `iters_per_launch` iterations
 // (pass A + pass B each) and reads back the 128-byte state after each launch;
 // nothing else crosses the host-device boundary during the iteration.
@@ -146,6 +148,13 @@ static fw_status direct_objective(fw_seg* h, double* E) {
     return FW_OK;
 }
 
+// One GFW iteration: pass A, pass B, finish (3 launches).
+static void iteration(fw_seg* h) {
+    h->ops->passA(h->pd, h->st, h->stream);
+    h->ops->passB(h->pd, h->st, h->stream);
+    h->ops->finish(h->pd, h->st, h->stream);
+}
+
 static fw_status build_graph(fw_seg* h) {
     if (h->graph) {
         cudaGraphExecDestroy(h->graph);
@@ -154,8 +163,7 @@ static fw_status build_graph(fw_seg* h) {
     cudaGraph_t g = nullptr;
     FW_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
     for (int i = 0; i < h->opts.iters_per_launch; ++i) {
-        h->ops->passA(h->pd, h->st, h->stream);
-        h->ops->passB(h->pd, h->st, h->stream);
+        iteration(h);
     }
     cudaError_t e = cudaStreamEndCapture(h->stream, &g);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
@@ -298,20 +306,13 @@ fw_status fw_seg_solve(fw_seg* h, fw_seg_stats* stats) {
         const int remaining = h->opts.max_iters - h->h_state->iter;
         if (remaining >= m && h->graph) {
             FW_CUDA(cudaGraphLaunch(h->graph, h->stream));
-            h->launches += 2 * m;
+            h->launches += 3 * m;
         } else {
-            // direct launches; the tail (< m iterations left) ends with the final
-            // evaluation: pass A at the iteration cap applies the last step and stops
-            const int it = std::min(remaining, m);
-            for (int i = 0; i < it; ++i) {
-                h->ops->passA(h->pd, h->st, h->stream);
-                h->ops->passB(h->pd, h->st, h->stream);
-            }
-            h->launches += 2 * it;
-            if (remaining < m) {
-                h->ops->passA(h->pd, h->st, h->stream);
-                ++h->launches;
-            }
+            // direct launches; the tail (< m iterations left) ends with one more
+            // pass pair whose stop test, at the iteration cap, ends the solve
+            const int it = remaining >= m ? m : remaining + 1;
+            for (int i = 0; i < it; ++i) iteration(h);
+            h->launches += 3 * it;
             FW_TRY(launch_check("iteration kernels"));
         }
         FW_TRY(read_state(h));
@@ -332,11 +333,11 @@ fw_status fw_seg_reset(fw_seg* h) {
     return FW_OK;
 }
 
-fw_status fw_seg_profile(fw_seg* h, int32_t iters, double* ms_a, double* ms_b) {
+fw_status fw_seg_profile(fw_seg* h, int32_t iters, double* ms_a, double* ms_b, double* ms_f) {
     if (!h || iters < 1) return invalid("bad arguments");
-    cudaEvent_t ev[3];
+    cudaEvent_t ev[4];
     for (auto& e : ev) FW_CUDA(cudaEventCreate(&e));
-    double ta = 0.0, tb = 0.0;
+    double ta = 0.0, tb = 0.0, tf = 0.0;
     int done = 0;
     fw_status rc = FW_OK;
     for (int i = 0; i < iters; ++i) {
@@ -345,22 +346,27 @@ fw_status fw_seg_profile(fw_seg* h, int32_t iters, double* ms_a, double* ms_b) {
         cudaEventRecord(ev[1], h->stream);
         h->ops->passB(h->pd, h->st, h->stream);
         cudaEventRecord(ev[2], h->stream);
-        cudaError_t e = cudaEventSynchronize(ev[2]);
+        h->ops->finish(h->pd, h->st, h->stream);
+        cudaEventRecord(ev[3], h->stream);
+        cudaError_t e = cudaEventSynchronize(ev[3]);
         if (e != cudaSuccess) {
             rc = cuda_fail(e, "profile iteration");
             break;
         }
-        float a = 0.f, b = 0.f;
+        float a = 0.f, b = 0.f, f = 0.f;
         cudaEventElapsedTime(&a, ev[0], ev[1]);
         cudaEventElapsedTime(&b, ev[1], ev[2]);
+        cudaEventElapsedTime(&f, ev[2], ev[3]);
         ta += a;
         tb += b;
+        tf += f;
         ++done;
     }
     for (auto& e : ev) cudaEventDestroy(e);
     if (rc != FW_OK) return rc;
     if (ms_a) *ms_a = ta / done;
     if (ms_b) *ms_b = tb / done;
+    if (ms_f) *ms_f = tf / done;
     return flush(h);
 }
 
@@ -373,9 +379,8 @@ fw_status fw_seg_step(fw_seg* h, int32_t iters, fw_seg_stats* stats) {
     for (int i = 0; i < iters && !h->h_state->done; ++i) {
         const int R = h->opts.refresh_every;
         if (R > 0 && h->h_state->iter - h->last_refresh >= R) FW_TRY(refresh_lu(h));
-        h->ops->passA(h->pd, h->st, h->stream);
-        h->ops->passB(h->pd, h->st, h->stream);
-        h->launches += 2;
+        iteration(h);
+        h->launches += 3;
         FW_TRY(launch_check("iteration kernels"));
         FW_TRY(read_state(h));
     }

@@ -57,7 +57,7 @@ __global__ void k_validate(int64_t n, const int32_t* rp, const int32_t* col, con
 __global__ void __launch_bounds__(kBlock) k_state_init(ProbState* st, const double* part, int nb) {
     __shared__ double red[kBlock];
     double S[1];
-    sum_partials<1>(part, nb, S, red);
+    sum_partials<1>(part, nb, S, red);   // nb may exceed kBlock: loops
     if (threadIdx.x == 0) {
         ProbState z = {};
         z.status = 2;  // FW_PENDING
@@ -101,9 +101,11 @@ Ops* make_ops(int weight_dtype, int K) {
 }
 
 int tile_rows_for(int64_t n) {
-    const int64_t per = (n + kTilesTarget - 1) / kTilesTarget;
-    return int(round_up(std::max<int64_t>(per, 1), kBlock));
+    const int64_t sub = (n + kBlock - 1) / kBlock;               // 256-row sub-tiles
+    const int64_t per = (sub + kTilesTarget - 1) / kTilesTarget;  // sub-tiles per tile
+    return int(std::max<int64_t>(per, 1) * kBlock);
 }
+
 
 int default_lanes(double avg_padded_degree) {
     int L = 1;
@@ -181,7 +183,8 @@ size_t problem_bytes(const ProbLayout& lay, size_t te, size_t we, bool comb) {
     size_t b = a256(4 * (n + 1)) + a256(4 * size_t(lay.nnz_pad)) + a256(we * size_t(lay.nnz_pad));
     if (comb) b += a256(te * n);
     b += 3 * a256(te * np * K) + a256(n) + a256(n);
-    b += a256(8 * size_t(lay.ntiles) * kNumA) + a256(8 * size_t(lay.ntiles) * kNumB);
+    b += a256(8 * size_t(lay.ntiles) * kNumR);
+    b += a256(8 * (2 * kNumR + 1));
     return b;
 }
 
@@ -205,8 +208,8 @@ void place_problem(char* base, const ProbLayout& lay, size_t te, size_t we, cons
     pd.LS = take(te * np * K);
     pd.choice = reinterpret_cast<uint8_t*>(take(n));
     pd.fid = reinterpret_cast<const int8_t*>(take(n));
-    pd.partA = reinterpret_cast<double*>(take(8 * size_t(lay.ntiles) * kNumA));
-    pd.partB = reinterpret_cast<double*>(take(8 * size_t(lay.ntiles) * kNumB));
+    pd.part = reinterpret_cast<double*>(take(8 * size_t(lay.ntiles) * kNumR));
+    pd.acc = reinterpret_cast<unsigned long long*>(take(8 * (2 * kNumR + 1)));
     pd.n = int32_t(lay.n);
     pd.npad = int32_t(lay.npad);
     pd.K = lay.K;
@@ -268,6 +271,7 @@ fw_status restart_problem(Ops* ops, const ProbDesc& pd, ProbState* st, bool from
     double* opart = nullptr;
     FW_TRYS(t.get(&opart, 8 * size_t(nb)));
     if (!from_current) ops->reinit(pd, s);
+    FW_CUDA(cudaMemsetAsync(pd.acc, 0, 8 * (2 * kNumR + 1), s));
     ops->spmm(pd, pd.U, pd.LU, s);
     ops->objective(pd, pd.LU, opart, s);
     k_state_init<<<1, kBlock, 0, s>>>(st, opart, nb);

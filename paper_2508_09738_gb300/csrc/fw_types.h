@@ -6,9 +6,10 @@ namespace fw {
 
 constexpr int kBlock = 256;         // threads per block of every row / CSR kernel
 constexpr int kPadW = 4;            // CSR rows padded to a multiple of 4 entries (int4 loads)
-constexpr int kTilesTarget = 2432;  // a problem is cut into at most this many row tiles
+constexpr int kTilesTarget = 1216;  // a problem has at most this many row tiles (8 per SM)
 constexpr int kNumA = 5;            // row-pass partials: g, ||D||^2, sum w||D||^2, <D,LU>, |I|
 constexpr int kNumB = 1;            // CSR-pass partial: <D, L S>
+constexpr int kNumR = kNumA + kNumB;  // doubles per tile record (pass A fills 0..4, pass B 5)
 constexpr uint8_t kActiveBit = 0x80;  // bit 7 of the choice byte: row moved by the oracle
 
 // One problem on the device.  Every array is the problem's own (row-local
@@ -26,12 +27,13 @@ struct ProbDesc {
     void* LS;            // T[K][npad], L S of the last step
     uint8_t* choice;     // [n] class chosen by the last evaluation | kActiveBit
     const int8_t* fid;   // [n] fidelity class or -1
-    double* partA;       // [ntiles][kNumA]
-    double* partB;       // [ntiles][kNumB]
+    double* part;        // [ntiles][kNumR] per-tile partial sums (kept for the objective)
+    unsigned long long* acc;  // [2*kNumR + 1] Q64.64 totals of this iteration (lo, hi per
+                              // quantity) and a non-finite flag; exact and order-free
     int32_t n;           // rows
     int32_t npad;        // class stride of the SoA block (multiple of 32)
     int32_t K;           // classes
-    int32_t tile_rows;   // rows per tile (multiple of kBlock)
+    int32_t tile_rows;   // rows per tile (kBlock)
     int32_t ntiles;      // tiles of this problem
     int32_t lanes;       // lanes per CSR row (1..32, power of two)
     int32_t comb;        // 1: L = D - W (diag used), 0: L_s (unit diagonal)
@@ -60,8 +62,9 @@ struct ProbState {
     int32_t has_update;  // 1: alpha / choice / LS of the last step not yet applied
     int32_t done;        // 1: stop rule met, later passes skip this problem
     int32_t g0_set;
-    uint32_t cntA, cntB, cntF;  // arrival counters of the last-block reductions
-    uint32_t pad_;
+    uint32_t cnt;        // pass-B tiles arrived (last one reduces the records)
+    uint32_t cntF;       // flush tiles arrived
+    uint32_t pad0_, pad1_;
 };
 
 }  // namespace fw
