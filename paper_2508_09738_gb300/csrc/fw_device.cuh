@@ -203,14 +203,17 @@ __device__ __forceinline__ bool last_to_arrive(uint32_t* cnt, uint32_t total) {
 }
 
 // ------------------------------------------ exact order-free accumulation
-// A finite double v with |v| < 2^62 is added to a 128-bit two's-complement
+// A finite double v with |v| < 2^52 is added to a 128-bit two's-complement
 // fixed-point number with 64 fraction bits (lo, hi words): v = hi + frac with
 // hi = floor(v), frac in [0, 1) exactly, and frac * 2^64 truncated to an
 // integer (parts below 2^-64 are dropped).  The carry of the low-word add is
 // exact, so the total is the exact sum of the added values whatever the order
-// of the atomic operations.  Non-finite values raise the flag word instead.
+// of the atomic operations.  A problem has at most kTilesTarget (< 2^11) tiles,
+// so a total of values below 2^52 cannot overflow the signed high word.
+// Non-finite or larger values raise the flag word instead.
 __device__ __forceinline__ void fx_add(unsigned long long* acc, int q, double v) {
-    if (!isfinite(v) || fabs(v) >= 4.0e18) {
+    static_assert(kTilesTarget < 2048, "fixed-point totals assume < 2^11 tiles");
+    if (!isfinite(v) || fabs(v) >= 0x1p52) {
         atomicOr(&acc[2 * kNumR], 1ull);
         return;
     }
