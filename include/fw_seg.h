@@ -304,6 +304,53 @@ fw_status fw_srv_get_info(fw_srv *s, fw_srv_info *info);
 /* Stop the worker (requests still queued or resident are dropped) and free. */
 void fw_srv_destroy(fw_srv *s);
 
+/* ------------------------------------------------------------------------
+ * Allocation-free energy evaluation.
+ *
+ * The paper has no counterpart to this call: it is a service entry point.  It
+ * evaluates the objective E(U) of Sec. 2.1 (the energy of eq. gradgl_vv2,
+ * as fw_seg_objective does for a handle) for a graph and an iterate that are
+ * already in the caller's device memory, without allocating device memory.
+ * It is meant for callers that cannot allocate: a process whose device memory
+ * is held by another allocator (cudaMalloc would fail), or a loop that must
+ * not call cudaMalloc / cudaFree (they may synchronise the device).  Its
+ * scratch is a static device array of FW_NOALLOC_MAX_N doubles plus 256 bytes
+ * (8 MiB + 256 B per device, part of the library's module image).
+ *
+ * Arguments (all *_dev pointers are device memory on the current device, read
+ * only, owned by the caller):
+ *   n, K              1 <= n <= FW_NOALLOC_MAX_N, 2 <= K <= 32
+ *   row_ptr_dev[n+1], col_dev[nnz], w_dev[nnz]
+ *                     CSR of W with the conventions at the top of this file
+ *                     (int32 indices, FP64 weights); nnz = row_ptr[n].
+ *   U_dev             FP64, row-major n x K with row stride ldu >= K elements
+ *   labels_dev        int32[n]: fidelity class in [0, K) or -1 (no fidelity);
+ *                     NULL means no fidelity node
+ *   eps, omega0       as in fw_seg_opts (eps may be +inf)
+ *   laplacian         FW_LAPLACIAN_SYM (L_s) or FW_LAPLACIAN_COMB (D - W)
+ *   cuda_stream       stream of the work (NULL: the legacy default stream);
+ *                     the call synchronises it before returning
+ *   E_host            receives E(U), FP64 sums combined exactly across blocks,
+ *                     so the result is bitwise reproducible
+ * Errors: FW_ERR_UNSUPPORTED if n > FW_NOALLOC_MAX_N (nothing is launched);
+ * FW_ERR_INVALID_ARG for bad sizes, pointers, options or labels; FW_ERR_GRAPH
+ * for a row_ptr extent or column outside [0, nnz) / [0, n) (never read);
+ * FW_ERR_ISOLATED for a node of degree 0; FW_ERR_NUMERIC for a non-finite
+ * energy; FW_ERR_CUDA.  Symmetry of W is not checked.
+ * The first call on each device looks up the scratch array's address
+ * (cudaGetSymbolAddress, which may load the module's device data) and caches
+ * it; make that first call before any stream capture.  All calls on a device
+ * share its one scratch array: calls that overlap in time on the same device
+ * race and may return wrong values, so the caller serialises them.
+ * ---------------------------------------------------------------------- */
+#define FW_NOALLOC_MAX_N 1048576
+
+fw_status fw_energy_noalloc(int64_t n, int32_t K, const int32_t *row_ptr_dev,
+                            const int32_t *col_dev, const double *w_dev, int64_t nnz,
+                            const double *U_dev, int64_t ldu, const int32_t *labels_dev,
+                            double eps, double omega0, int32_t laplacian, void *cuda_stream,
+                            double *E_host);
+
 /* Message of the last error on the calling thread ("" if none). */
 const char *fw_seg_last_error(void);
 

@@ -131,6 +131,9 @@ _SIGS = {
                               POINTER(fw_seg_stats)]),
     "fw_srv_get_info": (c_int32, [c_void_p, POINTER(fw_srv_info)]),
     "fw_srv_destroy": (None, [c_void_p]),
+    "fw_energy_noalloc": (c_int32, [c_int64, c_int32, c_void_p, c_void_p, c_void_p, c_int64,
+                                    c_void_p, c_int64, c_void_p, c_double, c_double, c_int32,
+                                    c_void_p, POINTER(c_double)]),
 }
 
 # symbols every build of the library must export (checked by the CPU tests)
@@ -553,3 +556,23 @@ class Server:
 
     def info(self):
         return fw_srv_get_info(self.s)
+
+
+# ------------------------------------------------- allocation-free energy --
+
+FW_NOALLOC_MAX_N = 1048576
+
+
+def fw_energy_noalloc(n, K, row_ptr_dev, col_dev, w_dev, nnz, U_dev, ldu, labels_dev, eps,
+                      omega0, laplacian="sym", cuda_stream=None) -> float:
+    """E(U) for a graph and iterate already on the device (integer device
+    addresses, e.g. ``tensor.data_ptr()``; labels_dev may be 0/None)."""
+    lap = LAPLACIAN[laplacian] if isinstance(laplacian, str) else int(laplacian)
+    if cuda_stream is not None and not isinstance(cuda_stream, int):
+        cuda_stream = int(getattr(cuda_stream, "cuda_stream", cuda_stream))
+    E = c_double()
+    _check(lib().fw_energy_noalloc(int(n), int(K), c_void_p(row_ptr_dev), c_void_p(col_dev),
+                                   c_void_p(w_dev), int(nnz), c_void_p(U_dev), int(ldu),
+                                   c_void_p(labels_dev or None), float(eps), float(omega0), lap,
+                                   c_void_p(cuda_stream or None), ctypes.byref(E)))
+    return E.value

@@ -90,6 +90,24 @@ def test_invalid_arguments_rejected_before_device_use(libpath):
     assert e.value.status == Bd.FW_ERR_INVALID_ARG
 
 
+def test_noalloc_energy_host_checks(libpath):
+    """fw_energy_noalloc rejects sizes above its static scratch and bad
+    arguments on the host, before any device pointer is touched."""
+    from paper_2508_09738_gb300 import binding as Bd
+    fake = 0x1000                         # never dereferenced: the checks come first
+    with pytest.raises(Bd.FwError) as e:
+        Bd.fw_energy_noalloc(Bd.FW_NOALLOC_MAX_N + 1, 3, fake, fake, fake, 8, fake, 3, 0,
+                             50.0, 1000.0)
+    assert e.value.status == Bd.FW_ERR_UNSUPPORTED
+    assert str(Bd.FW_NOALLOC_MAX_N) in str(e.value)
+    with pytest.raises(Bd.FwError) as e:
+        Bd.fw_energy_noalloc(10, 1, fake, fake, fake, 8, fake, 3, 0, 50.0, 1000.0)
+    assert e.value.status == Bd.FW_ERR_INVALID_ARG
+    with pytest.raises(Bd.FwError) as e:
+        Bd.fw_energy_noalloc(10, 3, fake, fake, fake, 8, fake, 2, 0, 50.0, 1000.0)
+    assert e.value.status == Bd.FW_ERR_INVALID_ARG
+
+
 def test_product_code_never_imports_oracle():
     """The CUDA path and its binding share no code with the oracle."""
     for dirpath, _, files in os.walk(PKG):
