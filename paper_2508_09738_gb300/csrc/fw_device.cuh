@@ -113,7 +113,7 @@ template <> __device__ __forceinline__ double alpha_of<double>(const ProbState* 
 // ------------------------------------------------ bulk async copies (TMA)
 // 1-D cp.async.bulk global -> shared completing on an mbarrier.  Addresses
 // and sizes must be multiples of 16 bytes; callers guarantee it.
-constexpr long long kMbarSpins = 1ll << 26;   // bound of one mbarrier wait (seconds)
+constexpr unsigned long long kMbarWaitNs = 2000000000ull;   // bound of one mbarrier wait: 2 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -149,13 +149,21 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait for the phase of the given parity; false when the bound ran out.
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Wait for the phase of the given parity, bounded in time by kMbarWaitNs;
+// false when the bound ran out.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    for (long long i = 0; i < kMbarSpins; ++i) {
+    if (mbar_test(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer_ns();
+    for (int i = 0;; ++i) {
         if (mbar_test(bar, parity)) return true;
-        if (i > 8) __nanosleep(40);
+        if (i > 8) __nanosleep(64);
+        if ((i & 63) == 63 && globaltimer_ns() - t0 > kMbarWaitNs) return mbar_test(bar, parity);
     }
-    return false;
 }
 
 // ------------------------------------------------------- block reductions
@@ -204,37 +212,53 @@ __device__ __forceinline__ bool last_to_arrive(uint32_t* cnt, uint32_t total) {
 
 // ------------------------------------------ exact order-free accumulation
 // A finite double v with |v| < 2^52 is added to a 128-bit two's-complement
-// fixed-point number with 64 fraction bits (lo, hi words): v = hi + frac with
-// hi = floor(v), frac in [0, 1) exactly, and frac * 2^64 truncated to an
-// integer (parts below 2^-64 are dropped).  The carry of the low-word add is
-// exact, so the total is the exact sum of the added values whatever the order
-// of the atomic operations.  A problem has at most kTilesTarget (< 2^11) tiles,
-// so a total of values below 2^52 cannot overflow the signed high word.
-// Non-finite or larger values raise the flag word instead.
-__device__ __forceinline__ void fx_add(unsigned long long* acc, int q, double v) {
+// fixed-point number with 64 fraction bits (slot[0] = lo, slot[1] = hi):
+// v = hi + frac with hi = floor(v), frac in [0, 1) exactly, and frac * 2^64
+// truncated to an integer (parts below 2^-64 are dropped).  The carry of the
+// low-word add is exact, so the total is the exact sum of the added values
+// whatever the order of the atomic operations.  A problem has at most
+// kTilesTarget (< 2^11) tiles, so a total of values below 2^52 cannot
+// overflow the signed high word.  Non-finite or larger values raise *flag.
+__device__ __forceinline__ void fx_add(unsigned long long* slot, unsigned long long* flag,
+                                       double v) {
     static_assert(kTilesTarget < 2048, "fixed-point totals assume < 2^11 tiles");
     if (!isfinite(v) || fabs(v) >= 0x1p52) {
-        atomicOr(&acc[2 * kNumR], 1ull);
+        atomicOr(flag, 1ull);
         return;
     }
     const double fl = floor(v);
     const unsigned long long lo = __double2ull_rz(ldexp(v - fl, 64));
     const unsigned long long hi = static_cast<unsigned long long>(__double2ll_rz(fl));
-    const unsigned long long old = atomicAdd(&acc[2 * q], lo);
+    const unsigned long long old = atomicAdd(&slot[0], lo);
     const unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
-    atomicAdd(&acc[2 * q + 1], hi + carry);
+    atomicAdd(&slot[1], hi + carry);
 }
 
-__device__ __forceinline__ double fx_get(const unsigned long long* acc, int q) {
-    const long long hi = static_cast<long long>(__ldcg(&acc[2 * q + 1]));
-    const unsigned long long lo = __ldcg(&acc[2 * q]);
-    return double(hi) + ldexp(double(lo), -64);
+__device__ __forceinline__ unsigned long long* acc_slot(unsigned long long* acc, int copy, int q) {
+    return acc + (copy * kNumR + q) * kAccLine;
 }
 
-// Sum NQ per-thread values over the block (as block_partials) and add the
-// block total to the fixed-point accumulators acc[q0 .. q0+NQ).
+// Exact total of quantity q over the accumulator copies (128-bit sum), as a
+// double.
+__device__ __forceinline__ double fx_total(const unsigned long long* acc, int q) {
+    unsigned long long lo = 0ull, hi = 0ull;
+#pragma unroll
+    for (int c = 0; c < kAccCopies; ++c) {
+        const unsigned long long* sl = acc + (c * kNumR + q) * kAccLine;
+        const unsigned long long l = __ldcg(sl), h = __ldcg(sl + 1);
+        const unsigned long long lo2 = lo + l;
+        hi += h + (lo2 < lo ? 1ull : 0ull);
+        lo = lo2;
+    }
+    return double(static_cast<long long>(hi)) + ldexp(double(lo), -64);
+}
+
+// Sum NQ per-thread values over the block (FP32 warp butterfly, then the
+// warps in a fixed order) and add the block total of quantity q0+q to copy
+// `copy` of the fixed-point accumulators.
 template <typename T, int NQ>
-__device__ __forceinline__ void block_accumulate(const T (&v)[NQ], unsigned long long* acc, int q0) {
+__device__ __forceinline__ void block_accumulate(const T (&v)[NQ], unsigned long long* acc, int q0,
+                                                 int copy) {
     __shared__ T red[kBlock / 32][NQ];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -249,7 +273,7 @@ __device__ __forceinline__ void block_accumulate(const T (&v)[NQ], unsigned long
         T s = T(0);
 #pragma unroll
         for (int w = 0; w < kBlock / 32; ++w) s = add_(s, red[w][threadIdx.x]);
-        fx_add(acc, q0 + threadIdx.x, double(s));
+        fx_add(acc_slot(acc, copy, q0 + threadIdx.x), acc + kAccFlag, double(s));
     }
     __syncthreads();
 }
@@ -509,6 +533,10 @@ __device__ __forceinline__ bool passA_staged(const ProbDesc& pd, int r_begin, in
     int j = 0;
     for (int base = r_begin; base < r_end; base += kBlock, ++j) {
         const int buf = nstages > 1 ? (j & 1) : 0;
+        // one buffer: this sub-tile's copy is issued once the previous one has
+        // been consumed (the __syncthreads at the end of the last iteration)
+        if (nstages == 1 && j > 0 && threadIdx.x == 0)
+            stage_issue<T, KMAX>(pd, base, min(kBlock, r_end - base), upd, stage, &bars[0]);
         const int rows = min(kBlock, r_end - base);
         T* sU = stage + buf * stage_elems;
         T* sL = sU + KMAX * kBlock;
@@ -524,9 +552,18 @@ __device__ __forceinline__ bool passA_staged(const ProbDesc& pd, int r_begin, in
                                  stage + (buf ^ 1) * stage_elems, &bars[buf ^ 1]);
         }
         const uint32_t par = (phases >> buf) & 1u;
-        if (!mbar_wait(&bars[buf], par)) {
+        const bool got = mbar_wait(&bars[buf], par);
+        if (__syncthreads_or(!got)) {
+            // a copy did not arrive in time: wait (bounded) for the copies still
+            // in flight into this block's buffers, then leave the tile; the
+            // caller raises the problem's error flag
             ok = false;
-            mbar_wait(&bars[buf], par);
+            if (got || mbar_wait(&bars[buf], par)) phases ^= 1u << buf;
+            if (nstages > 1 && base + kBlock < r_end &&
+                mbar_wait(&bars[buf ^ 1], (phases >> (buf ^ 1)) & 1u))
+                phases ^= 1u << (buf ^ 1);
+            __syncthreads();
+            break;
         }
         phases ^= 1u << buf;
         if (t < rows) {
@@ -860,10 +897,14 @@ __device__ __forceinline__ void finish_iter(const ProbDesc& pd, ProbState* st,
 __device__ __forceinline__ void finish_from_acc(const ProbDesc& pd, ProbState* st) {
     double S[kNumR];
 #pragma unroll
-    for (int q = 0; q < kNumR; ++q) S[q] = fx_get(pd.acc, q);
-    if (__ldcg(&pd.acc[2 * kNumR])) S[0] = CUDART_NAN;
+    for (int q = 0; q < kNumR; ++q) S[q] = fx_total(pd.acc, q);
+    if (__ldcg(&pd.acc[kAccFlag])) S[0] = CUDART_NAN;
 #pragma unroll
-    for (int q = 0; q < 2 * kNumR + 1; ++q) pd.acc[q] = 0ull;
+    for (int c = 0; c < kAccCopies * kNumR; ++c) {
+        pd.acc[c * kAccLine] = 0ull;
+        pd.acc[c * kAccLine + 1] = 0ull;
+    }
+    pd.acc[kAccFlag] = 0ull;
     finish_iter(pd, st, S);
 }
 
@@ -882,7 +923,7 @@ __device__ __forceinline__ void tile_A(const ProbDesc& pd, ProbState* st, int ti
         threadIdx.x == 0)
         atomicExch(&st->err, 1);
     const T v[kNumA] = {acc.g, acc.nD, acc.nW, acc.tLU, acc.act};
-    block_accumulate<T, kNumA>(v, pd.acc, 0);
+    block_accumulate<T, kNumA>(v, pd.acc, 0, tile % kAccCopies);
 }
 
 // One row tile of pass B.  With LAST, the last tile of the problem to finish
@@ -897,7 +938,7 @@ __device__ __forceinline__ void tile_B(const ProbDesc& pd, ProbState* st, int ti
     T accq = T(0);
     passB_rows<T, WT, KMAX, RO>(pd, r0, r1, accq, sm_lane, sm_row);
     const T v[kNumB] = {accq};
-    block_accumulate<T, kNumB>(v, pd.acc, kNumA);
+    block_accumulate<T, kNumB>(v, pd.acc, kNumA, tile % kAccCopies);
     if (LAST && last_to_arrive(&st->cnt, pd.ntiles) && threadIdx.x == 0) {
         st->cnt = 0;
         finish_from_acc(pd, st);

@@ -32,7 +32,7 @@ public:
     virtual int kmax() const = 0;
     virtual void passA(const ProbDesc& pd, ProbState* st, cudaStream_t s) = 0;
     virtual void passB(const ProbDesc& pd, ProbState* st, cudaStream_t s) = 0;
-    // one block: reduce both passes' tile records, stop test, step
+    // one thread: read the exact totals, stop test, step
     virtual void finish(const ProbDesc& pd, ProbState* st, cudaStream_t s) = 0;
     virtual void flush(const ProbDesc& pd, ProbState* st, cudaStream_t s) = 0;
     virtual void grad(const ProbDesc& pd, ProbState* st, void* Gout, uint8_t* chout,

@@ -39,7 +39,8 @@ __global__ void __launch_bounds__(kBlock)
     }
 }
 
-// Pass B: one block per row tile; the last block forms q and the step.
+// Pass B: one block per row tile; each adds its tile total to the exact
+// accumulators (no block waits for another).
 template <typename T, typename WT, int KMAX>
 __global__ void __launch_bounds__(kBlock) k_passB(ProbDesc pd, ProbState* st) {
     if (ld_cg(&st->done)) return;
@@ -50,7 +51,9 @@ __global__ void __launch_bounds__(kBlock) k_passB(ProbDesc pd, ProbState* st) {
 }
 
 // One thread after pass B: read the iteration's totals (complete after the
-// kernel boundary), run the stop test and the step.
+// kernel boundary), run the stop test and the step.  (Doing this in the last
+// block of pass B instead costs every block a fence and an arrival, which
+// measured slower than this launch.)
 static __global__ void k_finish(ProbDesc pd, ProbState* st) {
     if (threadIdx.x == 0 && !ld_cg(&st->done)) finish_from_acc(pd, st);
 }

@@ -36,8 +36,9 @@ namespace fw {
 namespace {
 
 constexpr int64_t kNaMaxN = FW_NOALLOC_MAX_N;
+constexpr int kNaErrWord = kAccWords;           // graph / label error bits
 constexpr int kNaAccWords = 32;                 // 256 bytes of accumulator words
-constexpr int kNaErrWord = 2 * kNumR + 1;       // graph / label error bits
+static_assert(kNaErrWord < kNaAccWords, "accumulators exceed the scratch words");
 constexpr size_t kNaScratchBytes = size_t(kNaAccWords) * 8 + size_t(kNaMaxN) * 8;
 constexpr int kNaMaxBlocks = 1024;              // < 2^11 block totals (fx_add range)
 constexpr int kNaMaxDevices = 64;
@@ -120,7 +121,7 @@ k_na_energy(int64_t n, int64_t nnz, int K, const int32_t* __restrict__ rp,
         e_thr += 0.5 * quad + inv_eps * pen + (f >= 0 ? 0.5 * omega0 * fidt : 0.0);
     }
     const double v[1] = {e_thr};
-    block_accumulate<double, 1>(v, acc, 0);
+    block_accumulate<double, 1>(v, acc, 0, int(blockIdx.x % kAccCopies));
 }
 
 std::mutex g_na_mu;
@@ -198,7 +199,7 @@ extern "C" fw_status fw_energy_noalloc(int64_t n, int32_t K, const int32_t* row_
                                           ldu, labels_dev, std::isinf(eps) ? 0.0 : 1.0 / eps,
                                           omega0, laplacian == FW_LAPLACIAN_COMB ? 1 : 0, acc);
     FW_CUDA(cudaGetLastError());
-    unsigned long long h[kNaErrWord + 1];
+    unsigned long long h[kNaAccWords];
     FW_CUDA(cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, s));
     FW_CUDA(cudaStreamSynchronize(s));
 
@@ -212,10 +213,18 @@ extern "C" fw_status fw_energy_noalloc(int64_t n, int32_t K, const int32_t* row_
         return FW_ERR_ISOLATED;
     }
     if (err & kNaBadLabel) return na_invalid("fw_energy_noalloc: label outside [-1, K)");
-    if (h[2 * kNumR]) {
+    if (h[kAccFlag]) {
         set_error("fw_energy_noalloc: non-finite or out-of-range partial energy");
         return FW_ERR_NUMERIC;
     }
-    *E_host = double(static_cast<long long>(h[1])) + std::ldexp(double(h[0]), -64);
+    // exact 128-bit total of the accumulator copies of quantity 0
+    unsigned long long lo = 0ull, hi = 0ull;
+    for (int c = 0; c < kAccCopies; ++c) {
+        const unsigned long long l = h[c * kNumR * kAccLine], hw = h[c * kNumR * kAccLine + 1];
+        const unsigned long long lo2 = lo + l;
+        hi += hw + (lo2 < lo ? 1ull : 0ull);
+        lo = lo2;
+    }
+    *E_host = double(static_cast<long long>(hi)) + std::ldexp(double(lo), -64);
     return FW_OK;
 }

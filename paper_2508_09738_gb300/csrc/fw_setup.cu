@@ -183,8 +183,7 @@ size_t problem_bytes(const ProbLayout& lay, size_t te, size_t we, bool comb) {
     size_t b = a256(4 * (n + 1)) + a256(4 * size_t(lay.nnz_pad)) + a256(we * size_t(lay.nnz_pad));
     if (comb) b += a256(te * n);
     b += 3 * a256(te * np * K) + a256(n) + a256(n);
-    b += a256(8 * size_t(lay.ntiles) * kNumR);
-    b += a256(8 * (2 * kNumR + 1));
+    b += a256(8 * size_t(kAccWords));
     return b;
 }
 
@@ -208,8 +207,7 @@ void place_problem(char* base, const ProbLayout& lay, size_t te, size_t we, cons
     pd.LS = take(te * np * K);
     pd.choice = reinterpret_cast<uint8_t*>(take(n));
     pd.fid = reinterpret_cast<const int8_t*>(take(n));
-    pd.part = reinterpret_cast<double*>(take(8 * size_t(lay.ntiles) * kNumR));
-    pd.acc = reinterpret_cast<unsigned long long*>(take(8 * (2 * kNumR + 1)));
+    pd.acc = reinterpret_cast<unsigned long long*>(take(8 * size_t(kAccWords)));
     pd.n = int32_t(lay.n);
     pd.npad = int32_t(lay.npad);
     pd.K = lay.K;
@@ -271,7 +269,7 @@ fw_status restart_problem(Ops* ops, const ProbDesc& pd, ProbState* st, bool from
     double* opart = nullptr;
     FW_TRYS(t.get(&opart, 8 * size_t(nb)));
     if (!from_current) ops->reinit(pd, s);
-    FW_CUDA(cudaMemsetAsync(pd.acc, 0, 8 * (2 * kNumR + 1), s));
+    FW_CUDA(cudaMemsetAsync(pd.acc, 0, 8 * size_t(kAccWords), s));
     ops->spmm(pd, pd.U, pd.LU, s);
     ops->objective(pd, pd.LU, opart, s);
     k_state_init<<<1, kBlock, 0, s>>>(st, opart, nb);

@@ -9,8 +9,16 @@ constexpr int kPadW = 4;            // CSR rows padded to a multiple of 4 entrie
 constexpr int kTilesTarget = 1216;  // a problem has at most this many row tiles (8 per SM)
 constexpr int kNumA = 5;            // row-pass partials: g, ||D||^2, sum w||D||^2, <D,LU>, |I|
 constexpr int kNumB = 1;            // CSR-pass partial: <D, L S>
-constexpr int kNumR = kNumA + kNumB;  // doubles per tile record (pass A fills 0..4, pass B 5)
+constexpr int kNumR = kNumA + kNumB;  // accumulated quantities (pass A 0..4, pass B 5)
 constexpr uint8_t kActiveBit = 0x80;  // bit 7 of the choice byte: row moved by the oracle
+// Exact tile-total accumulators: kAccCopies copies of the kNumR Q64.64
+// quantities (lo, hi words, kAccLine words apart), then a non-finite flag.
+// Tile t adds into copy t % kAccCopies.  (Spreading the copies over separate
+// 128-byte lines measured no faster than one compact copy, so one is used.)
+constexpr int kAccCopies = 1;
+constexpr int kAccLine = 2;                               // 8-byte words per slot
+constexpr int kAccFlag = kAccCopies * kNumR * kAccLine;   // index of the flag word
+constexpr int kAccWords = kAccFlag + kAccLine;
 
 // One problem on the device.  Every array is the problem's own (row-local
 // indexing, column indices local to the problem); in a batch they are slices
@@ -27,9 +35,8 @@ struct ProbDesc {
     void* LS;            // T[K][npad], L S of the last step
     uint8_t* choice;     // [n] class chosen by the last evaluation | kActiveBit
     const int8_t* fid;   // [n] fidelity class or -1
-    double* part;        // [ntiles][kNumR] per-tile partial sums (kept for the objective)
-    unsigned long long* acc;  // [2*kNumR + 1] Q64.64 totals of this iteration (lo, hi per
-                              // quantity) and a non-finite flag; exact and order-free
+    unsigned long long* acc;  // [kAccWords] Q64.64 totals of this iteration (see kAccCopies)
+                              // and a non-finite flag; exact and order-free
     int32_t n;           // rows
     int32_t npad;        // class stride of the SoA block (multiple of 32)
     int32_t K;           // classes
@@ -62,7 +69,7 @@ struct ProbState {
     int32_t has_update;  // 1: alpha / choice / LS of the last step not yet applied
     int32_t done;        // 1: stop rule met, later passes skip this problem
     int32_t g0_set;
-    uint32_t cnt;        // pass-B tiles arrived (last one reduces the records)
+    uint32_t cnt;        // pass-B tiles arrived (the last one finishes the iteration)
     uint32_t cntF;       // flush tiles arrived
     uint32_t pad0_, pad1_;
 };

@@ -53,6 +53,15 @@ def test_lockstep_class_counts(K):
     lockstep(g, 4, weights="f64", tol=1e-9)
 
 
+def test_lockstep_fp64_single_stage_multi_subtile():
+    """FP64 with K > 16 keeps one staging buffer per block (two would not fit
+    in shared memory), and n > 1216 * 256 gives every row tile several 256-row
+    sub-tiles: each sub-tile's copy must be issued when the buffer is free."""
+    g = W.sbm(n=320_000, K=20, deg_in=8.0, deg_out=1.0, label_frac=0.01, seed=7)
+    recs = lockstep(g, 3, weights="f64", tol=1e-9, energy=False)
+    assert len(recs) == 3
+
+
 def test_lockstep_armijo(blobs2k):
     lockstep(blobs2k, 15, weights="f64", step="armijo", tol=1e-9)
 
