@@ -642,7 +642,10 @@ __device__ __forceinline__ bool passA_staged(const ProbDesc& pd, int r_begin, in
 // Stage 1 of the sparse passes: for each row of a 256-row sub-tile, `L` lanes
 // walk the padded CSR row in 4-entry chunks and accumulate into per-lane bins
 // in shared memory (`sm_lane`, one KP-strided slot per thread); the lanes of a
-// row then add their slots in lane order into `sm_row[row]`.
+// row then add their slots in lane order into `sm_row[row]`.  Warp w handles
+// exactly rows 32w .. 32w+31 of the sub-tile (32/L rows at a time), so the
+// row sums never leave the warp: __syncwarp orders them, and the caller needs
+// no block barrier before thread t reads sm_row[t].
 //   ONEHOT: bin[s_j] += w_ij            (pass B: row i of W^ S)
 //   else:   bin[k]  += w_ij * X[k][j]   (SpMM: row i of W^ X)
 // A lane keeps two chunks (8 entries) in flight: their column, weight and
@@ -669,11 +672,11 @@ __device__ __forceinline__ void csr_bins(const ProbDesc& pd, const T* __restrict
     const uint8_t* __restrict__ choice = pd.choice;
     const int tid = threadIdx.x;
     const int lane = tid & (L - 1);
-    const int grp = tid / L;
-    const int R = kBlock / L;
+    const int grp = tid / L;                    // lane group: its lanes are adjacent threads
+    const int wrow = (tid & ~31) + (tid & 31) / L;
     T* my = sm_lane + tid * KP;
     for (int j = 0; j < L; ++j) {
-        const int rl = grp + R * j;
+        const int rl = wrow + (32 / L) * j;     // a row of this warp's 32
         const int r = base + rl;
         T acc[KMAX];
 #pragma unroll
@@ -770,32 +773,38 @@ __device__ __forceinline__ void passB_rows(const ProbDesc& pd, int r_begin, int 
     const T* __restrict__ diag = static_cast<const T*>(pd.diag);
     for (int base = r_begin; base < r_end; base += kBlock) {
         csr_bins<T, WT, KMAX, true, RO>(pd, nullptr, base, r_end, sm_lane, sm_row);
-        __syncthreads();
+        // sm_row[t] was written by this thread's own warp
         const int r = base + threadIdx.x;
         if (r < r_end) {
             const uint8_t sv = ld_cg(pd.choice + r);
             const int si = sv & 0x7f;
+            const bool act = (sv & kActiveBit) != 0;
             const T dg = pd.comb ? diag[r] : T(1);
-            T ls[KMAX];
 #pragma unroll
             for (int k = 0; k < KMAX; ++k)
                 if (k < K) {
                     const T b = sm_row[threadIdx.x * KP + k];
-                    ls[k] = (k == si) ? sub_(dg, b) : -b;
-                    LSb[k * np + r] = ls[k];
+                    LSb[k * np + r] = (k == si) ? sub_(dg, b) : -b;
                 }
-            if (sv & kActiveBit) {
+            if (act) {
+                // all K loads first (one round trip), then <D_i, LS_i>; LS_i is
+                // re-formed from the row sums rather than kept in registers
+                T u[KMAX];
+#pragma unroll
+                for (int k = 0; k < KMAX; ++k)
+                    if (k < K) u[k] = ld_cg(Ub + k * np + r);
                 T qi = T(0);
 #pragma unroll
                 for (int k = 0; k < KMAX; ++k)
                     if (k < K) {
-                        const T d = sub_(k == si ? T(1) : T(0), ld_cg(Ub + k * np + r));
-                        qi = fma_(d, ls[k], qi);
+                        const T b = sm_row[threadIdx.x * KP + k];
+                        const T ls = (k == si) ? sub_(dg, b) : -b;
+                        qi = fma_(sub_(k == si ? T(1) : T(0), u[k]), ls, qi);
                     }
                 accq = add_(accq, qi);
             }
         }
-        __syncthreads();
+        __syncwarp();   // the warp's bins are reused by the next sub-tile
     }
 }
 
@@ -810,7 +819,6 @@ __device__ __forceinline__ void spmm_rows(const ProbDesc& pd, const T* __restric
     const T* __restrict__ diag = static_cast<const T*>(pd.diag);
     for (int base = r_begin; base < r_end; base += kBlock) {
         csr_bins<T, WT, KMAX, false, true>(pd, X, base, r_end, sm_lane, sm_row);
-        __syncthreads();
         const int r = base + threadIdx.x;
         if (r < r_end) {
             const T dg = pd.comb ? diag[r] : T(1);
@@ -820,7 +828,7 @@ __device__ __forceinline__ void spmm_rows(const ProbDesc& pd, const T* __restric
                     OUT[k * np + r] = sub_(mul_(dg, ld_cg(X + k * np + r)),
                                            sm_row[threadIdx.x * KP + k]);
         }
-        __syncthreads();
+        __syncwarp();
     }
 }
 
