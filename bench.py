@@ -406,6 +406,135 @@ def run_serving(args, rank, world, local):
 
 
 # ------------------------------------------------------------------ ours --
+# -------------------------------------------------------------- one shot --
+def run_oneshot(args, rank, world, local):
+    """One-Shot Frank-Wolfe (Alg. 4) on the 2048x2048 image at eps = 0.1: the
+    fused single-pass kernel, against the GFW iteration path that reaches the
+    same labels in one step (Cor. nonconvb2).  Replicas only for N > 1."""
+    name = "voronoi2048_oneshot"
+    c = W.CONFIGS[name]
+    if args.impl == "reference":
+        if rank == 0:
+            g = W.make_config_graph(name)
+            v, dt, _ = cpu_oracle_oneshot(g, c)
+            print(json.dumps({"impl": "reference", "metric": "one-shot segmentations/s",
+                              "value": v, "unit": "solves/s", "n_gpus": world,
+                              "higher_is_better": True, "config": {"workload": name},
+                              "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1,
+                                               "kind": "oracle",
+                                               "sample": f"one OSFW on the full image, {dt:.1f} s"},
+                              "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                                      "d2h_bytes_per_step": 0}}), flush=True)
+        return
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    from paper_2508_09738_gb300 import build as Bld
+    if rank == 0:
+        Bld.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2508_09738_gb300 import binding as B
+    g = W.make_config_graph(name)
+    weights = args.weights or c["weights"]
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    opts = dict(eps=c["eps"], omega0=c["omega0"], weight_dtype=weights, max_iters=c["iters"],
+                cuda_stream=stream.cuda_stream)
+    seg = B.Segmenter(g, **opts)
+    for _ in range(args.warmup):
+        seg.oneshot(with_labels=False)
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    kms = [seg.oneshot(with_labels=False)[1] for _ in range(args.steps)]
+    clk = clocks.stop()
+    value, t_s = whole_job_rate(args.steps, sum(kms) / 1000.0, world, "cuda")
+    lab, _ = seg.oneshot()
+    # the GFW path: reset + solve stops after its single step (alpha = 1)
+    gfw_ms = []
+    for _ in range(3):
+        seg.reset()
+        st = seg.solve()
+        gfw_ms.append(st.ms)
+    lab_gfw = seg.labels()
+    seg.close()
+    wb = {"f32": 4, "bf16": 2, "f64": 8}[weights]
+    nbytes = 4 * (g.n + 1) + (4 + wb) * g.nnz + g.n + 4 * g.n
+    mean_ms = float(np.mean(kms))
+    peaks = load_peaks()
+    achieved = nbytes / (mean_ms / 1000.0) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": ncu_traffic("k_osfw", name),
+                "kernel": "k_osfw", "peak_source": peaks["source"],
+                "algorithmic_bytes_per_launch": nbytes, "kernel_ms": {"k_osfw": mean_ms}}
+    e2e = None
+    if not args.no_e2e:
+        def pinned(a):
+            t = torch.empty(a.shape, dtype=getattr(torch, str(a.dtype)), pin_memory=True)
+            t.numpy()[...] = a
+            return t
+        rp, col, w, lb = (pinned(g.row_ptr), pinned(g.col), pinned(g.w), pinned(g.labels))
+        out = torch.empty(g.n, dtype=torch.int32, pin_memory=True)
+        o = B.fw_seg_default_opts(**opts)
+        steps_e2e = max(1, min(args.steps, 3))
+        t0 = time.perf_counter()
+        for _ in range(steps_e2e):
+            h = B.fw_seg_create(g.n, rp.numpy(), col.numpy(), w.numpy(), g.K, lb.numpy(), o)
+            _check = B.lib().fw_seg_oneshot(h.ptr, B.c_void_p(out.data_ptr()), None)
+            B.fw_seg_destroy(h)
+            if _check < 0:
+                raise B.FwError(_check, B.fw_seg_last_error())
+        dt = time.perf_counter() - t0
+        e2e_rate, _ = whole_job_rate(steps_e2e, dt, world, "cuda")
+        e2e = {"value": e2e_rate, "unit": "solves/s",
+               "h2d_bytes_per_step": int(4 * (g.n + 1) + 12 * g.nnz + 4 * g.n),
+               "d2h_bytes_per_step": int(4 * g.n), "steps": steps_e2e,
+               "includes": "create (H2D, validation, Laplacian assembly, L U_0), one-shot "
+                           "kernel, labels D2H, destroy"}
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    line = {
+        "metric": "one-shot segmentations/s", "value": value, "unit": "solves/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if weights == "f64" else "f32",
+        "data": "synthetic",
+        "config": {"workload": name, "n": g.n, "nnz": g.nnz, "K": g.K, "eps": c["eps"],
+                   "omega0": c["omega0"], "weights": weights,
+                   "l2": "inputs (CSR %.0f MB) larger than L2" % ((4 + wb) * g.nnz / 1e6),
+                   "parallelism": f"replicas x{world}"},
+        "gfw_one_step_ms": float(np.median(gfw_ms)),
+        "labels_equal_gfw": bool(np.array_equal(lab, lab_gfw)),
+        "clocks": clk, "e2e": e2e, "gpu_launches": args.steps, "roofline": roofline,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        v, dt, s_o = cpu_oracle_oneshot(g, c)
+        line["label_agreement"] = float(np.mean(lab == s_o))
+        line["cpu_baseline"] = {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                                "sample": f"one OSFW (Alg. 4) of the oracle on the full image "
+                                          f"(numpy/scipy FP64, one thread), {dt:.1f} s"}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def cpu_oracle_oneshot(g, c):
+    """Oracle OSFW on the whole graph (problem set-up not timed)."""
+    import oracle as O
+    P = O.make_problem(g, c["eps"], c["omega0"], c["weights"])
+    t0 = time.perf_counter()
+    _, s = O.osfw(P)
+    dt = time.perf_counter() - t0
+    return 1.0 / dt, dt, s
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -415,6 +544,8 @@ def main():
         return run_batched(args, rank, world, local)
     if args.workload == "serving":
         return run_serving(args, rank, world, local)
+    if args.workload == "oneshot":
+        return run_oneshot(args, rank, world, local)
     c = W.CONFIGS[args.workload]
     if args.impl == "reference":
         run_reference(args, c, rank)

@@ -135,6 +135,17 @@ fw_status fw_seg_step(fw_seg *h, int32_t iters, fw_seg_stats *stats);
 /* Segmentation: labels_host[i] = argmax_k u_ik (lowest index on ties). */
 fw_status fw_seg_labels(fw_seg *h, int32_t *labels_host);
 
+/* One-Shot Frank-Wolfe (Alg. 4): U_1 = S_0 = GLMO(grad E(U_0)) from the start
+ * point U_0 = U_hat (Sec. 5.1), i.e. label_i = s_i, the class the (G)LMO picks
+ * for row i at U_hat (the handle's oracle option: greedy GLMO or full LMO).
+ * One fused pass over the CSR forms L U_hat from the fidelity data, the
+ * gradient and the argmin; the handle's iterate is neither read nor changed.
+ * The labels are bitwise the choices the iteration makes at U_0.  For eps
+ * below the bound of Cor. nonconvb2, GFW stops after this one step and the two
+ * coincide.  labels_host (n entries) may be NULL: the labels then stay on the
+ * device.  ms (nullable) receives the kernel's device time in milliseconds. */
+fw_status fw_seg_oneshot(fw_seg *h, int32_t *labels_host, double *ms);
+
 /* Copy U (n x K, row-major, widened to double) to the host. */
 fw_status fw_seg_get_U(fw_seg *h, double *U_host);
 

@@ -18,6 +18,7 @@ paper "A Greedy Frank-Wolfe for multiclass data segmentation"
   * LMO over the simplex product Sigma                      (Sec. 4, Alg. 2)
   * GLMO, the greedy row rule                        (Sec. 4, eq. eq:LMOpr)
   * GFW iteration                                           (Sec. 4, Alg. 3)
+  * One-Shot Frank-Wolfe, U_1 = GLMO(grad E(U_0))          (Sec. 4, Alg. 4)
   * FW gap g_k = -<grad E(U_k), D_k>             (Thm th:nonconvb; Sec. 5.1)
   * Armijo step (eqs. eta, Armijo; delta=0.5, gamma=1e-6 in Sec. 5.1)
   * U_0 = U_hat with unlabelled rows at 1/K                         (Sec. 5.1)
@@ -51,7 +52,7 @@ __all__ = [
     "round_weights", "degrees", "normalized_weights", "laplacian", "fidelity",
     "Problem", "make_problem", "energy", "gradient", "lmo", "glmo", "fw_gap",
     "hessian_apply", "curvature", "exact_step", "armijo_step", "Iterate",
-    "gfw_iteration", "gfw_solve", "labels_from_U",
+    "gfw_iteration", "gfw_solve", "osfw", "labels_from_U",
 ]
 
 
@@ -311,6 +312,22 @@ def gfw_solve(P: Problem, max_iters: int = 500, tol: float = 0.0,
         U = U + it.alpha * it.D
         iters += 1
     return U, dict(iters=iters, status=status, g0=g0, g=it.g, hist=hist)
+
+
+def osfw(P: Problem, oracle: str = "greedy", U0: Optional[np.ndarray] = None):
+    """One-Shot Frank-Wolfe (Alg. 4): from U_0 (U_hat unless given), take the
+    (G)LMO vertex of the gradient at U_0 as the result, U_1 = S_0.
+
+    Returns (U1, s): the vertex and the chosen class per row (its labels)."""
+    U = P.Uhat.copy() if U0 is None else np.array(U0, dtype=np.float64)
+    G = gradient(U, P)
+    if oracle == "greedy":
+        S, s, _ = glmo(G, U)
+    elif oracle == "full":
+        S, s = lmo(G)
+    else:
+        raise ValueError(oracle)
+    return S, s
 
 
 def labels_from_U(U: np.ndarray) -> np.ndarray:

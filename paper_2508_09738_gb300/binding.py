@@ -103,6 +103,7 @@ _SIGS = {
     "fw_seg_solve": (c_int32, [c_void_p, POINTER(fw_seg_stats)]),
     "fw_seg_step": (c_int32, [c_void_p, c_int32, POINTER(fw_seg_stats)]),
     "fw_seg_labels": (c_int32, [c_void_p, c_void_p]),
+    "fw_seg_oneshot": (c_int32, [c_void_p, c_void_p, POINTER(c_double)]),
     "fw_seg_get_U": (c_int32, [c_void_p, c_void_p]),
     "fw_seg_set_U": (c_int32, [c_void_p, c_void_p]),
     "fw_seg_get_grad": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
@@ -234,6 +235,14 @@ def fw_seg_labels(h: Handle, out: np.ndarray = None) -> np.ndarray:
     return out
 
 
+def fw_seg_oneshot(h: Handle, with_labels: bool = True):
+    """One-Shot Frank-Wolfe labels (Alg. 4) and the kernel's device ms."""
+    out = np.empty(h.n, dtype=np.int32) if with_labels else None
+    ms = c_double()
+    _check(lib().fw_seg_oneshot(h.ptr, _ptr(out), ctypes.byref(ms)))
+    return out, ms.value
+
+
 def fw_seg_get_U(h: Handle) -> np.ndarray:
     U = np.empty((h.n, h.K), dtype=np.float64)
     _check(lib().fw_seg_get_U(h.ptr, _ptr(U)))
@@ -317,6 +326,10 @@ class Segmenter:
 
     def step(self, iters=1):
         return fw_seg_step(self.h, iters)
+
+    def oneshot(self, with_labels=True):
+        """(labels, kernel ms) of One-Shot Frank-Wolfe (Alg. 4) from U_hat."""
+        return fw_seg_oneshot(self.h, with_labels)
 
     def labels(self):
         return fw_seg_labels(self.h)

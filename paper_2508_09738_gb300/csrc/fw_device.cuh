@@ -658,10 +658,24 @@ __device__ __forceinline__ V ld_gather(const V* p) {
     else return *p;
 }
 
-template <typename T, typename WT, int KMAX, bool ONEHOT, bool RO>
+// Value of U_hat (Sec. 2, the start point U_0 of Sec. 5.1) at class k of a row
+// with fidelity class f: e_f for a fidelity row, 1/K everywhere otherwise --
+// the same expression k_reinit stores, so products with it are bitwise those
+// of the stored U_0.
+template <typename T>
+__device__ __forceinline__ T uhat_val(int f, int k, T unif) {
+    return f >= 0 ? (k == f ? T(1) : T(0)) : unif;
+}
+
+// Gather sources of csr_bins: the one-hot S of the choice bytes (pass B), a
+// dense class-major X (SpMM), or U_hat formed from the fidelity bytes (OSFW).
+enum { kSrcOneHot = 0, kSrcDense = 1, kSrcUhat = 2 };
+
+template <typename T, typename WT, int KMAX, int SRC, bool RO>
 __device__ __forceinline__ void csr_bins(const ProbDesc& pd, const T* __restrict__ X, int base,
                                          int r_end, T* __restrict__ sm_lane,
                                          T* __restrict__ sm_row) {
+    constexpr bool ONEHOT = SRC == kSrcOneHot;
     constexpr int KP = KMAX | 1;
     const int K = pd.K;
     const int L = pd.lanes;
@@ -733,7 +747,7 @@ __device__ __forceinline__ void csr_bins(const ProbDesc& pd, const T* __restrict
 #pragma unroll
                     for (int t = 0; t < 8; ++t)
                         if (t < nt) my[sj[t]] = add_(my[sj[t]], v[t]);
-                } else {
+                } else if constexpr (SRC == kSrcDense) {
 #pragma unroll
                     for (int t = 0; t < 8; ++t) {
                         if (t < nt) {
@@ -741,6 +755,19 @@ __device__ __forceinline__ void csr_bins(const ProbDesc& pd, const T* __restrict
                             for (int k = 0; k < KMAX; ++k)
                                 if (k < K)
                                     acc[k] = fma_(v[t], ld_gather<RO>(X + k * np + cc[t]), acc[k]);
+                        }
+                    }
+                } else {
+                    const T unif = T(1) / T(K);
+                    int fj[8];
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) fj[t] = __ldg(pd.fid + cc[t]);
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) {
+                        if (t < nt) {
+#pragma unroll
+                            for (int k = 0; k < KMAX; ++k)
+                                if (k < K) acc[k] = fma_(v[t], uhat_val<T>(fj[t], k, unif), acc[k]);
                         }
                     }
                 }
@@ -772,7 +799,7 @@ __device__ __forceinline__ void passB_rows(const ProbDesc& pd, int r_begin, int 
     T* __restrict__ LSb = static_cast<T*>(pd.LS);
     const T* __restrict__ diag = static_cast<const T*>(pd.diag);
     for (int base = r_begin; base < r_end; base += kBlock) {
-        csr_bins<T, WT, KMAX, true, RO>(pd, nullptr, base, r_end, sm_lane, sm_row);
+        csr_bins<T, WT, KMAX, kSrcOneHot, RO>(pd, nullptr, base, r_end, sm_lane, sm_row);
         // sm_row[t] was written by this thread's own warp
         const int r = base + threadIdx.x;
         if (r < r_end) {
@@ -818,7 +845,7 @@ __device__ __forceinline__ void spmm_rows(const ProbDesc& pd, const T* __restric
     const int64_t np = pd.npad;
     const T* __restrict__ diag = static_cast<const T*>(pd.diag);
     for (int base = r_begin; base < r_end; base += kBlock) {
-        csr_bins<T, WT, KMAX, false, true>(pd, X, base, r_end, sm_lane, sm_row);
+        csr_bins<T, WT, KMAX, kSrcDense, true>(pd, X, base, r_end, sm_lane, sm_row);
         const int r = base + threadIdx.x;
         if (r < r_end) {
             const T dg = pd.comb ? diag[r] : T(1);
@@ -827,6 +854,58 @@ __device__ __forceinline__ void spmm_rows(const ProbDesc& pd, const T* __restric
                 if (k < K)
                     OUT[k * np + r] = sub_(mul_(dg, ld_cg(X + k * np + r)),
                                            sm_row[threadIdx.x * KP + k]);
+        }
+        __syncwarp();
+    }
+}
+
+// One-Shot Frank-Wolfe (Alg. 4) for rows [r_begin, r_end): U_1 = GLMO(grad
+// E(U_0)) at U_0 = U_hat, so label_i = s_i.  L U_hat is formed in the CSR pass
+// from the fidelity bytes (the SpMM of the stored U_0, same operation order),
+// and G', the binary/support tests and the argmin are those of pass A at U_0,
+// so s_i is bitwise the choice the iteration makes at U_0.
+template <typename T, typename WT, int KMAX>
+__device__ __forceinline__ void osfw_rows(const ProbDesc& pd, int32_t* __restrict__ labels,
+                                          int r_begin, int r_end, T* sm_lane, T* sm_row) {
+    constexpr int KP = KMAX | 1;
+    const int K = pd.K;
+    const T* __restrict__ diag = static_cast<const T*>(pd.diag);
+    const T c2 = c2_of<T>(pd);
+    const T om = om_of<T>(pd);
+    const T unif = T(1) / T(K);
+    const bool greedy = pd.oracle == 0;
+    for (int base = r_begin; base < r_end; base += kBlock) {
+        csr_bins<T, WT, KMAX, kSrcUhat, true>(pd, nullptr, base, r_end, sm_lane, sm_row);
+        const int r = base + threadIdx.x;
+        if (r < r_end) {
+            const int f = __ldg(pd.fid + r);
+            const T dg = pd.comb ? diag[r] : T(1);
+            bool binary = true;
+            T best = inf_<T>();
+            int s = -1, first_adm = -1, first_one = -1;
+#pragma unroll
+            for (int k = 0; k < KMAX; ++k)
+                if (k < K) {
+                    const T u = uhat_val<T>(f, k, unif);
+                    const T lu = sub_(mul_(dg, u), sm_row[threadIdx.x * KP + k]);
+                    binary = binary && (u == T(0) || u == T(1));
+                    if (first_one < 0 && u == T(1)) first_one = k;
+                    T gk = fma_(-c2, u, lu);
+                    if (f >= 0) gk = fma_(om, sub_(u, k == f ? T(1) : T(0)), gk);
+                    const bool adm = !greedy || u > T(0);
+                    if (adm && first_adm < 0) first_adm = k;
+                    if (adm && gk < best) {
+                        best = gk;
+                        s = k;
+                    }
+                }
+            const bool active = greedy ? !binary : true;
+            if (active) {
+                if (s < 0) s = first_adm < 0 ? 0 : first_adm;
+            } else {
+                s = first_one < 0 ? 0 : first_one;
+            }
+            labels[r] = s;
         }
         __syncwarp();
     }

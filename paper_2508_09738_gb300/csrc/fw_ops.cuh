@@ -28,6 +28,9 @@ public:
         e = cudaFuncSetAttribute(k_passB<T, WT, KMAX>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem()));
         if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(k_osfw<T, WT, KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 int(smem()));
+        if (e != cudaSuccess) return e;
         return cudaFuncSetAttribute(k_spmm<T, WT, KMAX>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem()));
     }
@@ -46,6 +49,9 @@ public:
     }
     void finish(const ProbDesc& pd, ProbState* st, cudaStream_t s) override {
         k_finish<<<1, 32, 0, s>>>(pd, st);
+    }
+    void oneshot(const ProbDesc& pd, int32_t* labels, cudaStream_t s) override {
+        k_osfw<T, WT, KMAX><<<pd.ntiles, kBlock, smem(), s>>>(pd, labels);
     }
     void spmm(const ProbDesc& pd, const void* X, void* out, cudaStream_t s) override {
         k_spmm<T, WT, KMAX><<<pd.ntiles, kBlock, smem(), s>>>(pd, (const T*)X, (T*)out);

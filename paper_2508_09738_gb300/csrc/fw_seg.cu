@@ -405,6 +405,24 @@ fw_status fw_seg_labels(fw_seg* h, int32_t* labels_host) {
     return FW_OK;
 }
 
+fw_status fw_seg_oneshot(fw_seg* h, int32_t* labels_host, double* ms) {
+    if (!h) return invalid("handle is NULL");
+    FW_CUDA(cudaEventRecord(h->ev0, h->stream));
+    h->ops->oneshot(h->pd, h->d_labels, h->stream);
+    FW_TRY(launch_check("one-shot kernel"));
+    FW_CUDA(cudaEventRecord(h->ev1, h->stream));
+    if (labels_host)
+        FW_CUDA(cudaMemcpyAsync(labels_host, h->d_labels, 4 * size_t(h->lay.n),
+                                cudaMemcpyDeviceToHost, h->stream));
+    FW_CUDA(cudaStreamSynchronize(h->stream));
+    if (ms) {
+        float t = 0.f;
+        FW_CUDA(cudaEventElapsedTime(&t, h->ev0, h->ev1));
+        *ms = t;
+    }
+    return FW_OK;
+}
+
 fw_status fw_seg_get_U(fw_seg* h, double* U_host) {
     if (!h || !U_host) return invalid("NULL argument");
     try {

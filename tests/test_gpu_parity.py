@@ -124,14 +124,17 @@ def test_free_running_sbm200k_vs_stored_oracle():
 
 def test_voronoi2048_one_shot_closed_form():
     """eps < 1: alpha_0 = 1 and the result is the row argmin of L_s U_hat on the
-    unlabelled pixels (Alg. 4 / Cor. nonconvb2)."""
+    unlabelled pixels (Alg. 4 / Cor. nonconvb2); the fused one-shot kernel
+    gives bitwise the labels of that GFW step."""
     c = W.CONFIGS["voronoi2048_oneshot"]
     g = W.make_config_graph("voronoi2048_oneshot")
     with B.Segmenter(g, eps=c["eps"], omega0=c["omega0"], weight_dtype="f32",
                      max_iters=c["iters"]) as s:
+        lab1, _ = s.oneshot()
         st = s.solve()
         lab = s.labels()
         U = s.U()
+    assert np.array_equal(lab1, lab)
     assert st.status == B.FW_OK and st.iters == 1 and st.alpha == 1.0
     assert np.all((U == 0) | (U == 1))
     P = O.make_problem(g, c["eps"], c["omega0"], "f32")
@@ -144,6 +147,67 @@ def test_voronoi2048_one_shot_closed_form():
     assert np.array_equal(lab[unl & safe], target[unl & safe])
     assert agreement(lab[unl], target[unl]) >= 0.999
     assert np.array_equal(lab[~unl], g.labels[~unl])
+
+
+# ---------------------------------------------------------------- OSFW --
+
+def _safe_rows(P, margin=1e-5):
+    """Rows whose best two entries of L U_hat differ by more than rounding."""
+    part = np.sort(P.L @ P.Uhat, axis=1)
+    return (part[:, 1] - part[:, 0]) > margin * np.maximum(1.0, np.abs(part[:, 0]))
+
+
+@pytest.mark.parametrize("oracle", ["greedy", "full"])
+@pytest.mark.parametrize("weights", ["f64", "f32", "bf16"])
+def test_oneshot_equals_first_choice(blobs2k, weights, oracle):
+    """OSFW (Alg. 4): the labels are bitwise the (G)LMO choices the iteration
+    makes at U_0 = U_hat, the iterate is untouched, and the oracle's OSFW
+    agrees."""
+    with B.Segmenter(blobs2k, eps=50.0, omega0=1000.0, weight_dtype=weights,
+                     oracle=oracle) as s:
+        U0 = s.U()
+        lab, ms = s.oneshot()
+        _, ch, _ = s.grad()
+        assert np.array_equal(lab, ch)
+        assert np.array_equal(s.U(), U0) and s.stats().iters == 0 and ms > 0
+        assert s.step(3).iters == 3
+    P = O.make_problem(blobs2k, 50.0, 1000.0, weights)
+    _, s_o = O.osfw(P, oracle=oracle)
+    safe = _safe_rows(P)
+    assert np.array_equal(lab[safe], s_o[safe])
+    assert agreement(lab, s_o) >= 0.999
+
+
+@pytest.mark.parametrize("K", [2, 5, 13, 32])
+def test_oneshot_class_counts_ragged(K):
+    g = W.blobs_knn(n=40 * K + 3, K=K, seed=200 + K, label_frac=0.1)
+    for wd in ("f32", "f64"):
+        with B.Segmenter(g, weight_dtype=wd) as s:
+            lab, _ = s.oneshot()
+            _, ch, _ = s.grad()
+            assert np.array_equal(lab, ch), (K, wd)
+
+
+def test_oneshot_comb_laplacian(blobs2k):
+    with B.Segmenter(blobs2k, laplacian="comb", eps=float("inf"), oracle="full",
+                     weight_dtype="f64") as s:
+        lab, _ = s.oneshot()
+        _, ch, _ = s.grad()
+        assert np.array_equal(lab, ch)
+
+
+def test_oneshot_sbm200k_vs_oracle():
+    c = W.CONFIGS["sbm200k"]
+    g = W.make_config_graph("sbm200k")
+    with B.Segmenter(g, eps=c["eps"], omega0=c["omega0"], weight_dtype=c["weights"]) as s:
+        lab, _ = s.oneshot()
+        _, ch, _ = s.grad()
+    assert np.array_equal(lab, ch)
+    P = O.make_problem(g, c["eps"], c["omega0"], c["weights"])
+    _, s_o = O.osfw(P)
+    safe = _safe_rows(P)
+    assert np.array_equal(lab[safe], s_o[safe])
+    assert agreement(lab, s_o) >= 0.999
 
 
 # ---------------------------------------------------------- edge cases --

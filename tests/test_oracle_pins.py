@@ -167,6 +167,41 @@ def test_one_shot_closed_form(gen):
     assert np.array_equal(O.labels_from_U(U)[unl], target[unl])
     assert np.array_equal(O.labels_from_U(U)[~unl], g.labels[~unl])
     assert np.all((U == 0) | (U == 1))
+    # Cor. nonconvb2: for such eps GFW is OSFW (Alg. 4)
+    U1, s1 = O.osfw(P)
+    assert np.array_equal(U1, U) and np.array_equal(s1, O.labels_from_U(U))
+
+
+# OSFW at any eps (Alg. 4): at U_hat the penalty gradient (1/eps)(1 - 2u) is
+# the same for every class of an unlabelled row and the fidelity gradient is
+# zero, so S_0 = GLMO(grad E(U_hat)) picks argmin_k (L_s U_hat)_ik on the
+# unlabelled rows (lowest index) and keeps every labelled row; checked against
+# an independent dense L_s, at an eps where GFW does not stop after one step.
+@pytest.mark.parametrize("oracle", ["greedy", "full"])
+def test_osfw_any_eps_closed_form(oracle):
+    g = W.blobs_knn(n=350, K=4, seed=23, label_frac=0.05)
+    P = O.make_problem(g, 50.0, 1000.0)
+    A = dense_W(g)
+    d = A.sum(1)
+    Ls = np.eye(g.n) - A / np.sqrt(np.outer(d, d))
+    LU = Ls @ P.Uhat
+    U1, s = O.osfw(P, oracle=oracle)
+    unl = g.labels < 0
+    assert np.all((U1 == 0) | (U1 == 1)) and np.all(U1.sum(1) == 1)
+    assert np.array_equal(s, O.labels_from_U(U1))
+    assert np.array_equal(s[unl], np.argmin(LU, axis=1)[unl])
+    if oracle == "greedy":
+        assert np.array_equal(s[~unl], g.labels[~unl])
+    else:
+        # full LMO at U_hat: a labelled row adds omega_0 (u - e_c) = 0 and
+        # (1/eps)(1 - 2u), which is -1/eps on its class and +1/eps elsewhere
+        G = LU + (1.0 - 2.0 * P.Uhat) / 50.0
+        assert np.array_equal(s[~unl], np.argmin(G, axis=1)[~unl])
+    # the first GFW iteration chooses the same classes (Alg. 3 step 2)
+    it = O.gfw_iteration(P.Uhat, P, oracle=oracle)
+    assert np.array_equal(it.s, s)
+    # and GFW at this eps does not end after that step
+    assert 0.0 < it.alpha < 1.0
 
 
 # ------------------------------------------------------------------ P4 --
