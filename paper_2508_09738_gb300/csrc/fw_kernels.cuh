@@ -59,14 +59,15 @@ static __global__ void k_finish(ProbDesc pd, ProbState* st) {
 }
 
 // One-Shot Frank-Wolfe (Alg. 4): labels of U_1 = GLMO(grad E(U_hat)) in one
-// CSR pass; the iterate arrays are not touched.
+// CSR pass; the iterate arrays are not touched.  There is no reduction, so
+// each block takes one 256-row sub-tile (fine-grained, no tail wave).
 template <typename T, typename WT, int KMAX>
 __global__ void __launch_bounds__(kBlock) k_osfw(ProbDesc pd, int32_t* labels) {
     extern __shared__ __align__(128) unsigned char smraw[];
     T* sm_lane = reinterpret_cast<T*>(smraw);
     T* sm_row = sm_lane + kBlock * (KMAX | 1);
-    const int r0 = blockIdx.x * pd.tile_rows;
-    const int r1 = min(pd.n, r0 + pd.tile_rows);
+    const int r0 = blockIdx.x * kBlock;
+    const int r1 = min(pd.n, r0 + kBlock);
     osfw_rows<T, WT, KMAX>(pd, labels, r0, r1, sm_lane, sm_row);
 }
 

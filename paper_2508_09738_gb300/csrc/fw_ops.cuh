@@ -51,7 +51,7 @@ public:
         k_finish<<<1, 32, 0, s>>>(pd, st);
     }
     void oneshot(const ProbDesc& pd, int32_t* labels, cudaStream_t s) override {
-        k_osfw<T, WT, KMAX><<<pd.ntiles, kBlock, smem(), s>>>(pd, labels);
+        k_osfw<T, WT, KMAX><<<rows_grid(pd), kBlock, smem(), s>>>(pd, labels);
     }
     void spmm(const ProbDesc& pd, const void* X, void* out, cudaStream_t s) override {
         k_spmm<T, WT, KMAX><<<pd.ntiles, kBlock, smem(), s>>>(pd, (const T*)X, (T*)out);
