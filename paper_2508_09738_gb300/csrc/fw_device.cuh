@@ -758,6 +758,11 @@ __device__ __forceinline__ void csr_bins(const ProbDesc& pd, const T* __restrict
                         }
                     }
                 } else {
+                    // the SpMM of U_hat, entry by entry: an unlabelled neighbour
+                    // adds v/K to every class (one fma each), a labelled one
+                    // adds v to its class only -- fma(v, 1, a) = a + v and
+                    // fma(v, 0, a) = a exactly, so the sums are bitwise those
+                    // of fma(v, U_hat[j][k], a) over every class
                     const T unif = T(1) / T(K);
                     int fj[8];
 #pragma unroll
@@ -765,9 +770,15 @@ __device__ __forceinline__ void csr_bins(const ProbDesc& pd, const T* __restrict
 #pragma unroll
                     for (int t = 0; t < 8; ++t) {
                         if (t < nt) {
+                            if (fj[t] < 0) {
 #pragma unroll
-                            for (int k = 0; k < KMAX; ++k)
-                                if (k < K) acc[k] = fma_(v[t], uhat_val<T>(fj[t], k, unif), acc[k]);
+                                for (int k = 0; k < KMAX; ++k)
+                                    if (k < K) acc[k] = fma_(v[t], unif, acc[k]);
+                            } else {
+#pragma unroll
+                                for (int k = 0; k < KMAX; ++k)
+                                    if (k == fj[t]) acc[k] = add_(acc[k], v[t]);
+                            }
                         }
                     }
                 }
