@@ -154,16 +154,26 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
+// try_wait with a suspend-time hint: the thread sleeps in hardware until the
+// phase completes or about `ns` nanoseconds pass, instead of re-issuing polls.
+__device__ __forceinline__ bool mbar_test_sleep(uint64_t* bar, uint32_t parity, uint32_t ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(ns)
+        : "memory");
+    return ok != 0;
+}
 // Wait for the phase of the given parity, bounded in time by kMbarWaitNs;
 // false when the bound ran out.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    if (mbar_test(bar, parity)) return true;
+    if (mbar_test_sleep(bar, parity, 20000u)) return true;
     const unsigned long long t0 = globaltimer_ns();
-    for (int i = 0;; ++i) {
-        if (mbar_test(bar, parity)) return true;
-        if (i > 8) __nanosleep(64);
-        if ((i & 63) == 63 && globaltimer_ns() - t0 > kMbarWaitNs) return mbar_test(bar, parity);
-    }
+    while (globaltimer_ns() - t0 <= kMbarWaitNs)
+        if (mbar_test_sleep(bar, parity, 20000u)) return true;
+    return mbar_test(bar, parity);
 }
 
 // ------------------------------------------------------- block reductions

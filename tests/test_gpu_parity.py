@@ -210,6 +210,32 @@ def test_oneshot_sbm200k_vs_oracle():
     assert agreement(lab, s_o) >= 0.999
 
 
+# ------------------------------------------------- warm start (f3) --
+
+@pytest.mark.parametrize("weights,tol", [("f64", 1.0), ("f32", 0.999)])
+def test_warm_start_inference_on_new_nodes(weights, tol):
+    """Sec. 4, last paragraph: old rows start at their binary labels, added
+    rows at 1/K; the old rows stay bitwise fixed, only the new rows are active,
+    and their labels match the oracle's run from the same start."""
+    g = W.blobs_knn(n=3000, K=5, seed=43, label_frac=0.03)
+    rng = np.random.default_rng(6)
+    new = np.zeros(g.n, bool)
+    new[rng.choice(g.n, 300, replace=False)] = True
+    new &= g.labels < 0
+    U0 = np.full((g.n, g.K), 1.0 / g.K)
+    U0[~new] = np.eye(g.K)[g.truth[~new]]
+    with B.Segmenter(g, eps=50.0, omega0=1000.0, weight_dtype=weights, max_iters=150) as s:
+        s.set_U(U0)
+        st = s.solve()
+        U = s.U()
+        lab = s.labels()
+    assert st.iters > 0 and st.active_rows <= int(new.sum())
+    assert np.array_equal(U[~new], U0[~new])
+    P = O.make_problem(g, 50.0, 1000.0, weights)
+    Uo, info = O.gfw_solve(P, max_iters=150, U0=U0)
+    assert agreement(lab[new], O.labels_from_U(Uo)[new]) >= tol
+
+
 # ---------------------------------------------------------- edge cases --
 
 def test_hand_example_path3():

@@ -438,3 +438,24 @@ def test_labels_lowest_index_tie():
     _, s, act = O.glmo(G, U)
     # row 0: class 2 is outside supp, tie on {0,1} -> 0; row 1: tie -> 1; row 2 binary
     assert s.tolist() == [0, 1, 2] and act.tolist() == [True, True, False]
+
+
+# ------------------------------------------------------------------ f3 --
+# Warm-start inference on added nodes (Sec. 4, last paragraph): start from a
+# point whose old rows are the binary solution of the old data and whose new
+# rows are at 1/K.  A binary row is never active under the GLMO, so the old
+# rows stay exactly as they were and only the new rows move.
+def test_warm_start_new_nodes_only():
+    g = W.blobs_knn(n=600, K=4, seed=41, label_frac=0.05)
+    rng = np.random.default_rng(5)
+    new = np.zeros(g.n, bool)
+    new[rng.choice(g.n, 60, replace=False)] = True
+    new &= g.labels < 0
+    P = O.make_problem(g, 50.0, 1000.0)
+    U0 = np.full((g.n, g.K), 1.0 / g.K)
+    U0[~new] = np.eye(g.K)[g.truth[~new]]
+    U, info = O.gfw_solve(P, max_iters=60, U0=U0, record=True)
+    assert np.array_equal(U[~new], U0[~new])
+    assert max(info["hist"]["active"]) <= int(new.sum())
+    assert np.any(U[new] != U0[new])
+    assert info["iters"] > 0
