@@ -164,6 +164,14 @@ fw_status fw_seg_get_grad(fw_seg *h, double *G_host, int32_t *choice_host,
 /* E(U) at the current iterate, evaluated directly (fresh L U product). */
 fw_status fw_seg_objective(fw_seg *h, double *E);
 
+/* Diagnostic: the classic Frank-Wolfe gap of the full LMO (Alg. 2) at the
+ * current iterate, sum_i sum_k u_ik (G_ik - min_j G_ij) with G = grad E(U)
+ * from a fresh L U product.  It is 0 exactly at a stationary point of E over
+ * Sigma and never below the GLMO gap g_k of the iteration (which is 0 at any
+ * binary point, stationary or not).  FP64 sum of per-block partials in a
+ * fixed order. */
+fw_status fw_seg_lmo_gap(fw_seg *h, double *gap);
+
 /* Recompute L U from scratch (drift control for the recurrence). */
 fw_status fw_seg_refresh(fw_seg *h);
 

@@ -20,6 +20,7 @@ paper "A Greedy Frank-Wolfe for multiclass data segmentation"
   * GFW iteration                                           (Sec. 4, Alg. 3)
   * One-Shot Frank-Wolfe, U_1 = GLMO(grad E(U_0))          (Sec. 4, Alg. 4)
   * FW gap g_k = -<grad E(U_k), D_k>             (Thm th:nonconvb; Sec. 5.1)
+  * classic (full-LMO) FW gap, the stationarity measure        (Sec. 4, Alg. 2)
   * Armijo step (eqs. eta, Armijo; delta=0.5, gamma=1e-6 in Sec. 5.1)
   * U_0 = U_hat with unlabelled rows at 1/K                         (Sec. 5.1)
 
@@ -50,7 +51,7 @@ import scipy.sparse as sp
 
 __all__ = [
     "round_weights", "degrees", "normalized_weights", "laplacian", "fidelity",
-    "Problem", "make_problem", "energy", "gradient", "lmo", "glmo", "fw_gap",
+    "Problem", "make_problem", "energy", "gradient", "lmo", "glmo", "fw_gap", "lmo_gap",
     "hessian_apply", "curvature", "exact_step", "armijo_step", "Iterate",
     "gfw_iteration", "gfw_solve", "osfw", "labels_from_U",
 ]
@@ -212,6 +213,14 @@ def fw_gap(G: np.ndarray, U: np.ndarray, s: np.ndarray, active: np.ndarray) -> f
     Gs = G[np.arange(G.shape[0]), s]
     terms = U * (G - Gs[:, None])
     return float(np.sum(terms[active]))
+
+
+def lmo_gap(G: np.ndarray, U: np.ndarray) -> float:
+    """Classic FW gap of the full LMO (Alg. 2): <G, U - S> with S = LMO(G),
+    summed termwise as sum_i sum_k u_ik (G_ik - min_j G_ij); every term is
+    >= 0, and the sum is 0 exactly at a stationary point of E over Sigma."""
+    m = np.min(G, axis=1)
+    return float(np.sum(U * (G - m[:, None])))
 
 
 def curvature(D: np.ndarray, P: Problem) -> float:

@@ -109,6 +109,7 @@ _SIGS = {
     "fw_seg_get_grad": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "fw_seg_objective": (c_int32, [c_void_p, POINTER(c_double)]),
     "fw_seg_refresh": (c_int32, [c_void_p]),
+    "fw_seg_lmo_gap": (c_int32, [c_void_p, POINTER(c_double)]),
     "fw_seg_get_stats": (c_int32, [c_void_p, POINTER(fw_seg_stats)]),
     "fw_seg_reset": (c_int32, [c_void_p]),
     "fw_seg_profile": (c_int32, [c_void_p, c_int32, POINTER(c_double), POINTER(c_double),
@@ -264,6 +265,13 @@ def fw_seg_get_grad(h: Handle):
     return G, ch, act.astype(bool)
 
 
+def fw_seg_lmo_gap(h: Handle) -> float:
+    """Classic (full-LMO) FW gap at the current iterate (stationarity measure)."""
+    g = c_double()
+    _check(lib().fw_seg_lmo_gap(h.ptr, ctypes.byref(g)))
+    return g.value
+
+
 def fw_seg_objective(h: Handle) -> float:
     E = c_double()
     _check(lib().fw_seg_objective(h.ptr, ctypes.byref(E)))
@@ -342,6 +350,9 @@ class Segmenter:
 
     def grad(self):
         return fw_seg_get_grad(self.h)
+
+    def lmo_gap(self):
+        return fw_seg_lmo_gap(self.h)
 
     def objective(self):
         return fw_seg_objective(self.h)

@@ -126,6 +126,39 @@ __global__ void __launch_bounds__(kBlock) k_objective(ProbDesc pd, const T* LUf,
     block_partials<double, 1>(v, part + blockIdx.x);
 }
 
+// Classic (full-LMO) FW gap at U (Alg. 2), the stationarity measure over
+// Sigma: per row sum_k u_ik (G'_ik - min_j G'_ij) with G' from a freshly
+// computed LUf = L U (the constant 1/eps term cancels); FP64 block partials.
+template <typename T, int KMAX>
+__global__ void __launch_bounds__(kBlock) k_lmo_gap(ProbDesc pd, const T* LUf, double* part) {
+    const int r = blockIdx.x * kBlock + threadIdx.x;
+    double e = 0.0;
+    if (r < pd.n) {
+        const T* Ub = static_cast<const T*>(pd.U);
+        const int f = pd.fid[r];
+        const T c2 = c2_of<T>(pd);
+        const T om = om_of<T>(pd);
+        T u[KMAX], g[KMAX];
+        T mn = inf_<T>();
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k)
+            if (k < pd.K) {
+                u[k] = Ub[(int64_t)k * pd.npad + r];
+                T gk = fma_(-c2, u[k], LUf[(int64_t)k * pd.npad + r]);
+                if (f >= 0) gk = fma_(om, sub_(u[k], k == f ? T(1) : T(0)), gk);
+                g[k] = gk;
+                mn = gk < mn ? gk : mn;
+            }
+        T acc = T(0);
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k)
+            if (k < pd.K) acc = fma_(u[k], sub_(g[k], mn), acc);
+        e = double(acc);
+    }
+    const double v[1] = {e};
+    block_partials<double, 1>(v, part + blockIdx.x);
+}
+
 // Fresh iteration state: E_0 = fixed-order sum of the objective partials,
 // everything else zero, status FW_PENDING (one block).
 __global__ void __launch_bounds__(kBlock) k_state_init(ProbState* st, const double* part, int nb);

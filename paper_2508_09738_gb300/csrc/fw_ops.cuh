@@ -69,6 +69,9 @@ public:
     void labels(const ProbDesc& pd, int32_t* out, cudaStream_t s) override {
         k_labels<T><<<rows_grid(pd), kBlock, 0, s>>>(pd, out);
     }
+    void lmo_gap(const ProbDesc& pd, const void* LUf, double* part, cudaStream_t s) override {
+        k_lmo_gap<T, KMAX><<<rows_grid(pd), kBlock, 0, s>>>(pd, (const T*)LUf, part);
+    }
     void objective(const ProbDesc& pd, const void* LUf, double* part, cudaStream_t s) override {
         k_objective<T><<<rows_grid(pd), kBlock, 0, s>>>(pd, (const T*)LUf, part);
     }

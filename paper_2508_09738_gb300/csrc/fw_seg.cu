@@ -505,6 +505,29 @@ fw_status fw_seg_objective(fw_seg* h, double* E) {
     }
 }
 
+fw_status fw_seg_lmo_gap(fw_seg* h, double* gap) {
+    if (!h || !gap) return invalid("NULL argument");
+    try {
+        FW_TRY(flush(h));
+        h->ops->spmm(h->pd, h->pd.U, h->d_tmp, h->stream);
+        h->ops->lmo_gap(h->pd, h->d_tmp, h->d_opart, h->stream);
+        h->launches += 2;
+        FW_TRY(launch_check("LMO gap kernels"));
+        const int64_t nb = (h->lay.n + kBlock - 1) / kBlock;
+        std::vector<double> part(size_t(nb), 0.0);
+        FW_CUDA(cudaMemcpyAsync(part.data(), h->d_opart, sizeof(double) * nb,
+                                cudaMemcpyDeviceToHost, h->stream));
+        FW_CUDA(cudaStreamSynchronize(h->stream));
+        double s = 0.0;
+        for (double x : part) s += x;
+        *gap = s;
+        return FW_OK;
+    } catch (const std::bad_alloc&) {
+        set_error("host allocation failed");
+        return FW_ERR_NO_MEMORY;
+    }
+}
+
 fw_status fw_seg_refresh(fw_seg* h) {
     if (!h) return invalid("handle is NULL");
     FW_TRY(read_state(h));

@@ -210,6 +210,40 @@ def test_oneshot_sbm200k_vs_oracle():
     assert agreement(lab, s_o) >= 0.999
 
 
+# ---------------------------------------------------------- LMO gap --
+
+@pytest.mark.parametrize("weights,tol", [("f64", 1e-9), ("f32", TOL)])
+def test_lmo_gap_diagnostic(blobs2k, weights, tol):
+    """Classic (full-LMO) FW gap at the GPU iterate against the oracle's at
+    the same U; never below the iteration's GLMO gap."""
+    with B.Segmenter(blobs2k, eps=50.0, omega0=1000.0, weight_dtype=weights,
+                     max_iters=10 ** 6) as s:
+        for k in (0, 25):
+            if k:
+                s.step(k)
+            gl = s.lmo_gap()
+            U = s.U()
+            P = O.make_problem(blobs2k, 50.0, 1000.0, weights)
+            G = O.gradient(U, P)
+            go = O.lmo_gap(G, U)
+            assert rel(gl, go) <= tol, (k, gl, go)
+            _, s_o, act_o = O.glmo(G, U)
+            assert gl >= O.fw_gap(G, U, s_o, act_o) * (1 - 1e-6)
+
+
+def test_lmo_gap_zero_at_one_shot_vertex():
+    """eps < 1: every vertex is stationary, so after the one GFW step (alpha = 1,
+    a binary U) the classic FW gap is exactly 0, as in the oracle."""
+    g = W.voronoi_image(side=64, K=3, seed=9, label_frac=0.01)
+    with B.Segmenter(g, eps=0.1, omega0=1e5, weight_dtype="f32", max_iters=10) as s:
+        st = s.solve()
+        assert st.iters == 1
+        assert s.lmo_gap() == 0.0
+        U = s.U()
+    P = O.make_problem(g, 0.1, 1e5, "f32")
+    assert O.lmo_gap(O.gradient(U, P), U) == 0.0
+
+
 # ------------------------------------------------- warm start (f3) --
 
 @pytest.mark.parametrize("weights,tol", [("f64", 1.0), ("f32", 0.999)])

@@ -357,6 +357,8 @@ def test_linear_solve_special_case():
         Ek = O.energy(U, P) - Estar
         # convex E: the FW gap bounds the primal error; line search is monotone
         assert -1e-12 <= Ek <= it.g + 1e-10
+        # with the full LMO every row is active, so g is the classic FW gap
+        assert abs(O.lmo_gap(it.G, U) - it.g) <= 1e-12 * max(1.0, it.g)
         assert Ek <= Eprev + 1e-12
         Eprev = Ek
         U = U + it.alpha * it.D
@@ -459,3 +461,32 @@ def test_warm_start_new_nodes_only():
     assert max(info["hist"]["active"]) <= int(new.sum())
     assert np.any(U[new] != U0[new])
     assert info["iters"] > 0
+
+
+# ------------------------------------------------------------ LMO gap --
+# The classic FW gap of the full LMO is the stationarity measure over Sigma:
+# (i) it is never below the GLMO gap (the GLMO minimises over the support
+# only and leaves binary rows out); (ii) for eps < 1 the penalty term makes
+# every vertex stationary: at a binary row with class c, G_ic carries -1/eps
+# and every other class +1/eps, and 2/eps exceeds the spread of (L_s U)_i,
+# whose entries lie in [-1, 2] on Sigma -- so the gap is 0 at every vertex.
+def test_lmo_gap_bounds_and_vertex_stationarity():
+    rng = np.random.default_rng(91)
+    g = W.blobs_knn(n=300, K=4, seed=92, label_frac=0.05)
+    P = O.make_problem(g, 50.0, 1000.0)
+    for _ in range(5):
+        U = random_simplex_rows(g.n, g.K, rng)
+        G = O.gradient(U, P)
+        _, s, act = O.glmo(G, U)
+        assert O.lmo_gap(G, U) >= O.fw_gap(G, U, s, act) - 1e-12
+    U, _ = O.gfw_solve(P, max_iters=30)
+    it = O.gfw_iteration(U, P)
+    assert O.lmo_gap(it.G, U) >= it.g - 1e-12
+    # a binary point: GLMO gap 0 by construction, LMO gap 0 only if stationary
+    Pe = O.make_problem(g, 0.1, 1000.0)
+    for _ in range(3):
+        V = np.eye(g.K)[rng.integers(0, g.K, g.n)]
+        V[g.labels >= 0] = np.eye(g.K)[g.labels[g.labels >= 0]]
+        assert O.lmo_gap(O.gradient(V, Pe), V) == 0.0
+    # at eps = 50 a random vertex is not stationary
+    assert O.lmo_gap(O.gradient(V, P), V) > 0.0
