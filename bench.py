@@ -169,10 +169,10 @@ def run_reference(args, c, rank):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000 * total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": config_dict(args, c, g, iters),
+        "config": config_dict(args, c, g, args.iters or c["iters"]),
         "cpu_baseline": {"value": v, "unit": "iter/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{iters} GFW iterations from U_0 per step (numpy/scipy FP64, "
-                                   f"one thread)"},
+                         "sample": f"each step: the first {iters} GFW iterations from U_0 of "
+                                   f"that solve (numpy/scipy FP64, one thread)"},
         "e2e": {"value": v, "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
