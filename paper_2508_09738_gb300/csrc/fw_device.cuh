@@ -524,11 +524,13 @@ __device__ __forceinline__ void stage_issue(const ProbDesc& pd, int base, int ro
     }
 }
 
-template <typename T, int KMAX>
+// EXACT: the problem has exactly KMAX classes, so every per-class guard of
+// the unrolled loops is known at compile time.
+template <typename T, int KMAX, bool EXACT = false>
 __device__ __forceinline__ bool passA_staged(const ProbDesc& pd, int r_begin, int r_end, bool upd,
                                              T alpha, AccA<T>& acc, T* stage, int nstages,
                                              uint64_t* bars, uint32_t& phases) {
-    const int K = pd.K;
+    const int K = EXACT ? KMAX : pd.K;
     const int64_t np = pd.npad;
     T* __restrict__ Ub = static_cast<T*>(pd.U);
     T* __restrict__ LUb = static_cast<T*>(pd.LU);
@@ -1020,14 +1022,14 @@ __device__ __forceinline__ void finish_from_acc(const ProbDesc& pd, ProbState* s
 // One row tile of pass A with its block reduction; the last tile of the
 // problem to finish runs the stop test.  `ndone` (nullable) counts problems
 // that stop in this pass.  Every thread of the block must call it.
-template <typename T, int KMAX>
+template <typename T, int KMAX, bool EXACT = false>
 __device__ __forceinline__ void tile_A(const ProbDesc& pd, ProbState* st, int tile, bool upd,
                                        T alpha, T* stage, int nstages, uint64_t* bars,
                                        uint32_t& phases) {
     const int r0 = tile * pd.tile_rows;
     const int r1 = min(pd.n, r0 + pd.tile_rows);
     AccA<T> acc{T(0), T(0), T(0), T(0), T(0)};
-    if (!passA_staged<T, KMAX>(pd, r0, r1, upd, alpha, acc, stage, nstages, bars, phases) &&
+    if (!passA_staged<T, KMAX, EXACT>(pd, r0, r1, upd, alpha, acc, stage, nstages, bars, phases) &&
         threadIdx.x == 0)
         atomicExch(&st->err, 1);
     const T v[kNumA] = {acc.g, acc.nD, acc.nW, acc.tLU, acc.act};

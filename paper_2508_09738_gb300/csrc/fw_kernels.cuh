@@ -39,6 +39,27 @@ __global__ void __launch_bounds__(kBlock)
     }
 }
 
+// Pass A (step) for exactly four classes with an FP32 iterate: the class loop
+// is fully known at compile time, which removes the per-class guards, and the
+// kernel is held to 32 registers so that 8 blocks per SM stay resident.
+template <typename T>
+__global__ void __launch_bounds__(kBlock, 8) k_passA_k4(ProbDesc pd, ProbState* st) {
+    extern __shared__ __align__(128) unsigned char smraw[];
+    __shared__ __align__(8) uint64_t bars[2];
+    if (ld_cg(&st->done)) return;
+    const bool upd = ld_cg(&st->has_update) != 0;
+    const T alpha = alpha_of<T>(st);
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+    }
+    __syncthreads();
+    uint32_t phases = 0;
+    const int nst = (pd.tile_rows > kBlock && max_stages<T, 4>() == 2) ? 2 : 1;
+    tile_A<T, 4, true>(pd, st, blockIdx.x, upd, alpha, reinterpret_cast<T*>(smraw), nst, bars,
+                       phases);
+}
+
 // Pass B: one block per row tile; each adds its tile total to the exact
 // accumulators (no block waits for another).
 template <typename T, typename WT, int KMAX>

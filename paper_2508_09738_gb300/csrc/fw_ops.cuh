@@ -8,6 +8,8 @@ namespace fw {
 template <typename T, typename WT, int KMAX>
 class OpsImpl final : public Ops {
 public:
+    // four classes, FP32 iterate: the compile-time class-count pass A
+    static constexpr bool kExact4 = KMAX == 4 && sizeof(T) == 4;
     size_t elem() const override { return sizeof(T); }
     size_t welem() const override { return sizeof(WT); }
     int kmax() const override { return KMAX; }
@@ -25,6 +27,11 @@ public:
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              int(smemA()));
         if (e != cudaSuccess) return e;
+        if constexpr (kExact4) {
+            e = cudaFuncSetAttribute(k_passA_k4<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     int(smemA()));
+            if (e != cudaSuccess) return e;
+        }
         e = cudaFuncSetAttribute(k_passB<T, WT, KMAX>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem()));
         if (e != cudaSuccess) return e;
@@ -35,7 +42,11 @@ public:
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem()));
     }
     void passA(const ProbDesc& pd, ProbState* st, cudaStream_t s) override {
-        k_passA<T, KMAX, MODE_STEP><<<pd.ntiles, kBlock, smemA(pd), s>>>(pd, st, nullptr, nullptr);
+        if (kExact4 && pd.K == 4)
+            k_passA_k4<T><<<pd.ntiles, kBlock, smemA(pd), s>>>(pd, st);
+        else
+            k_passA<T, KMAX, MODE_STEP><<<pd.ntiles, kBlock, smemA(pd), s>>>(pd, st, nullptr,
+                                                                             nullptr);
     }
     void flush(const ProbDesc& pd, ProbState* st, cudaStream_t s) override {
         k_passA<T, KMAX, MODE_FLUSH><<<pd.ntiles, kBlock, 0, s>>>(pd, st, nullptr, nullptr);
