@@ -71,6 +71,16 @@ __global__ void __launch_bounds__(kBlock) k_passB(ProbDesc pd, ProbState* st) {
     tile_B<T, WT, KMAX, true, false>(pd, st, blockIdx.x, sm_lane, sm_row, nullptr);
 }
 
+// Pass B with one lane per row known at compile time (low-degree graphs such
+// as images); EXACT for exactly KMAX classes.  Same sums as k_passB.
+template <typename T, typename WT, int KMAX, bool EXACT>
+__global__ void __launch_bounds__(kBlock) k_passB_l1(ProbDesc pd, ProbState* st) {
+    if (ld_cg(&st->done)) return;
+    extern __shared__ __align__(128) unsigned char smraw[];
+    T* sm_lane = reinterpret_cast<T*>(smraw);
+    tile_B<T, WT, KMAX, true, false, true, EXACT>(pd, st, blockIdx.x, sm_lane, sm_lane, nullptr);
+}
+
 // One thread after pass B: read the iteration's totals (complete after the
 // kernel boundary), run the stop test and the step.  (Doing this in the last
 // block of pass B instead costs every block a fence and an arrival, which

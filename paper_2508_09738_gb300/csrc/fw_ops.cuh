@@ -38,6 +38,14 @@ public:
         e = cudaFuncSetAttribute(k_osfw<T, WT, KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  int(smem()));
         if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(k_passB_l1<T, WT, KMAX, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem()));
+        if (e != cudaSuccess) return e;
+        if constexpr (kExact4) {
+            e = cudaFuncSetAttribute(k_passB_l1<T, WT, 4, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem()));
+            if (e != cudaSuccess) return e;
+        }
         return cudaFuncSetAttribute(k_spmm<T, WT, KMAX>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem()));
     }
@@ -56,7 +64,14 @@ public:
         k_passA<T, KMAX, MODE_GRAD><<<pd.ntiles, kBlock, 0, s>>>(pd, st, (T*)Gout, chout);
     }
     void passB(const ProbDesc& pd, ProbState* st, cudaStream_t s) override {
-        k_passB<T, WT, KMAX><<<pd.ntiles, kBlock, smem(), s>>>(pd, st);
+        if (pd.lanes == 1) {
+            if (kExact4 && pd.K == 4)
+                k_passB_l1<T, WT, 4, true><<<pd.ntiles, kBlock, smem(), s>>>(pd, st);
+            else
+                k_passB_l1<T, WT, KMAX, false><<<pd.ntiles, kBlock, smem(), s>>>(pd, st);
+        } else {
+            k_passB<T, WT, KMAX><<<pd.ntiles, kBlock, smem(), s>>>(pd, st);
+        }
     }
     void finish(const ProbDesc& pd, ProbState* st, cudaStream_t s) override {
         k_finish<<<1, 32, 0, s>>>(pd, st);
