@@ -683,18 +683,18 @@ __device__ __forceinline__ T uhat_val(int f, int k, T unif) {
 // dense class-major X (SpMM), or U_hat formed from the fidelity bytes (OSFW).
 enum { kSrcOneHot = 0, kSrcDense = 1, kSrcUhat = 2 };
 
-// L1: one lane per row known at compile time -- each thread's bins are its
-// own row's sums, so the lane-sum stage is skipped and the caller reads
-// sm_lane (a sum over one lane is the value itself, so nothing changes).
-// EXACT: the problem has exactly KMAX classes.
-template <typename T, typename WT, int KMAX, int SRC, bool RO, bool L1 = false, bool EXACT = false>
+// LC: lanes per row known at compile time (0: the runtime pd.lanes).  With one
+// lane each thread's bins are its own row's sums, so the lane-sum stage is
+// skipped and the caller reads sm_lane (a sum over one lane is the value
+// itself, so nothing changes).  EXACT: the problem has exactly KMAX classes.
+template <typename T, typename WT, int KMAX, int SRC, bool RO, int LC = 0, bool EXACT = false>
 __device__ __forceinline__ void csr_bins(const ProbDesc& pd, const T* __restrict__ X, int base,
                                          int r_end, T* __restrict__ sm_lane,
                                          T* __restrict__ sm_row) {
     constexpr bool ONEHOT = SRC == kSrcOneHot;
     constexpr int KP = KMAX | 1;
     const int K = EXACT ? KMAX : pd.K;
-    const int L = L1 ? 1 : pd.lanes;
+    const int L = LC ? LC : pd.lanes;
     const int64_t np = pd.npad;
     const int32_t* __restrict__ rp = pd.rp;
     const int32_t* __restrict__ col = pd.col;
@@ -805,7 +805,7 @@ __device__ __forceinline__ void csr_bins(const ProbDesc& pd, const T* __restrict
             for (int k = 0; k < KMAX; ++k)
                 if (k < K) my[k] = acc[k];
         }
-        if constexpr (!L1) {
+        if constexpr (LC != 1) {
             __syncwarp();
             for (int k = lane; k < K; k += L) {
                 T s = T(0);
@@ -818,18 +818,18 @@ __device__ __forceinline__ void csr_bins(const ProbDesc& pd, const T* __restrict
 }
 
 // Pass B over rows [r_begin, r_end): LS = L S (one-hot S) and sum_i <D_i, LS_i>.
-template <typename T, typename WT, int KMAX, bool RO, bool L1 = false, bool EXACT = false>
+template <typename T, typename WT, int KMAX, bool RO, int LC = 0, bool EXACT = false>
 __device__ __forceinline__ void passB_rows(const ProbDesc& pd, int r_begin, int r_end, T& accq,
                                            T* sm_lane, T* sm_row_in) {
     constexpr int KP = KMAX | 1;
     const int K = EXACT ? KMAX : pd.K;
-    T* const sm_row = L1 ? sm_lane : sm_row_in;   // one lane: its bins are the row sums
+    T* const sm_row = LC == 1 ? sm_lane : sm_row_in;   // one lane: its bins are the row sums
     const int64_t np = pd.npad;
     const T* __restrict__ Ub = static_cast<const T*>(pd.U);
     T* __restrict__ LSb = static_cast<T*>(pd.LS);
     const T* __restrict__ diag = static_cast<const T*>(pd.diag);
     for (int base = r_begin; base < r_end; base += kBlock) {
-        csr_bins<T, WT, KMAX, kSrcOneHot, RO, L1, EXACT>(pd, nullptr, base, r_end, sm_lane, sm_row);
+        csr_bins<T, WT, KMAX, kSrcOneHot, RO, LC, EXACT>(pd, nullptr, base, r_end, sm_lane, sm_row);
         // sm_row[t] was written by this thread's own warp
         const int r = base + threadIdx.x;
         if (r < r_end) {
@@ -1047,14 +1047,14 @@ __device__ __forceinline__ void tile_A(const ProbDesc& pd, ProbState* st, int ti
 // runs finish_iter on the accumulated totals (persistent kernel); otherwise a
 // separate k_finish launch does that.  `ndone` (nullable) counts problems
 // that stop.
-template <typename T, typename WT, int KMAX, bool RO, bool LAST, bool L1 = false,
+template <typename T, typename WT, int KMAX, bool RO, bool LAST, int LC = 0,
           bool EXACT = false>
 __device__ __forceinline__ void tile_B(const ProbDesc& pd, ProbState* st, int tile, T* sm_lane,
                                        T* sm_row, uint32_t* ndone) {
     const int r0 = tile * pd.tile_rows;
     const int r1 = min(pd.n, r0 + pd.tile_rows);
     T accq = T(0);
-    passB_rows<T, WT, KMAX, RO, L1, EXACT>(pd, r0, r1, accq, sm_lane, sm_row);
+    passB_rows<T, WT, KMAX, RO, LC, EXACT>(pd, r0, r1, accq, sm_lane, sm_row);
     const T v[kNumB] = {accq};
     block_accumulate<T, kNumB>(v, pd.acc, kNumA, tile % kAccCopies);
     if (LAST && last_to_arrive(&st->cnt, pd.ntiles) && threadIdx.x == 0) {

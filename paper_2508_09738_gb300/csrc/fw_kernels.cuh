@@ -71,14 +71,16 @@ __global__ void __launch_bounds__(kBlock) k_passB(ProbDesc pd, ProbState* st) {
     tile_B<T, WT, KMAX, true, false>(pd, st, blockIdx.x, sm_lane, sm_row, nullptr);
 }
 
-// Pass B with one lane per row known at compile time (low-degree graphs such
-// as images); EXACT for exactly KMAX classes.  Same sums as k_passB.
-template <typename T, typename WT, int KMAX, bool EXACT>
-__global__ void __launch_bounds__(kBlock) k_passB_l1(ProbDesc pd, ProbState* st) {
+// Pass B with LC lanes per row known at compile time (1 for low-degree graphs
+// such as images, 2 or 4 for denser ones); EXACT for exactly KMAX classes.
+// Same sums, in the same order, as k_passB.
+template <typename T, typename WT, int KMAX, int LC, bool EXACT>
+__global__ void __launch_bounds__(kBlock) k_passB_lc(ProbDesc pd, ProbState* st) {
     if (ld_cg(&st->done)) return;
     extern __shared__ __align__(128) unsigned char smraw[];
     T* sm_lane = reinterpret_cast<T*>(smraw);
-    tile_B<T, WT, KMAX, true, false, true, EXACT>(pd, st, blockIdx.x, sm_lane, sm_lane, nullptr);
+    T* sm_row = sm_lane + kBlock * (KMAX | 1);
+    tile_B<T, WT, KMAX, true, false, LC, EXACT>(pd, st, blockIdx.x, sm_lane, sm_row, nullptr);
 }
 
 // One thread after pass B: read the iteration's totals (complete after the

@@ -38,11 +38,13 @@ public:
         e = cudaFuncSetAttribute(k_osfw<T, WT, KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  int(smem()));
         if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(k_passB_l1<T, WT, KMAX, false>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem()));
-        if (e != cudaSuccess) return e;
+        for (auto f : {k_passB_lc<T, WT, KMAX, 1, false>, k_passB_lc<T, WT, KMAX, 2, false>,
+                       k_passB_lc<T, WT, KMAX, 4, false>}) {
+            e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem()));
+            if (e != cudaSuccess) return e;
+        }
         if constexpr (kExact4) {
-            e = cudaFuncSetAttribute(k_passB_l1<T, WT, 4, true>,
+            e = cudaFuncSetAttribute(k_passB_lc<T, WT, 4, 1, true>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem()));
             if (e != cudaSuccess) return e;
         }
@@ -64,14 +66,17 @@ public:
         k_passA<T, KMAX, MODE_GRAD><<<pd.ntiles, kBlock, 0, s>>>(pd, st, (T*)Gout, chout);
     }
     void passB(const ProbDesc& pd, ProbState* st, cudaStream_t s) override {
-        if (pd.lanes == 1) {
-            if (kExact4 && pd.K == 4)
-                k_passB_l1<T, WT, 4, true><<<pd.ntiles, kBlock, smem(), s>>>(pd, st);
-            else
-                k_passB_l1<T, WT, KMAX, false><<<pd.ntiles, kBlock, smem(), s>>>(pd, st);
-        } else {
-            k_passB<T, WT, KMAX><<<pd.ntiles, kBlock, smem(), s>>>(pd, st);
-        }
+        const unsigned g = unsigned(pd.ntiles);
+        if (pd.lanes == 1 && kExact4 && pd.K == 4)
+            k_passB_lc<T, WT, 4, 1, true><<<g, kBlock, smem(), s>>>(pd, st);
+        else if (pd.lanes == 1)
+            k_passB_lc<T, WT, KMAX, 1, false><<<g, kBlock, smem(), s>>>(pd, st);
+        else if (pd.lanes == 2)
+            k_passB_lc<T, WT, KMAX, 2, false><<<g, kBlock, smem(), s>>>(pd, st);
+        else if (pd.lanes == 4)
+            k_passB_lc<T, WT, KMAX, 4, false><<<g, kBlock, smem(), s>>>(pd, st);
+        else
+            k_passB<T, WT, KMAX><<<g, kBlock, smem(), s>>>(pd, st);
     }
     void finish(const ProbDesc& pd, ProbState* st, cudaStream_t s) override {
         k_finish<<<1, 32, 0, s>>>(pd, st);
