@@ -179,11 +179,12 @@ fw_status fw_seg_refresh(fw_seg *h);
  * after fw_seg_create.  Used to time repeated solves of one resident graph. */
 fw_status fw_seg_reset(fw_seg *h);
 
-/* Measurement: run `iters` iterations as separate launches with CUDA events
- * around each kernel on the handle's stream; the outputs (each nullable) get
- * the mean device time in milliseconds of pass A (update, gradient, GLMO, gap
- * pieces), pass B (one-hot L S, <D, L S>) and the finishing kernel (reduction
- * of both passes' tile records, stop test, line search).  The iterate advances. */
+/* Measurement: run `iters` (1..4096) iterations as separate launches, enqueued
+ * back to back on the handle's stream with a CUDA event between consecutive
+ * kernels (one host wait at the end); the outputs (each nullable) get the mean
+ * device time in milliseconds of pass A (update, gradient, GLMO, gap pieces),
+ * pass B (one-hot L S, <D, L S>) and the finishing kernel (exact totals, stop
+ * test, line search).  The iterate advances. */
 fw_status fw_seg_profile(fw_seg *h, int32_t iters, double *ms_row_pass, double *ms_csr_pass,
                          double *ms_finish);
 

@@ -334,39 +334,50 @@ fw_status fw_seg_reset(fw_seg* h) {
 }
 
 fw_status fw_seg_profile(fw_seg* h, int32_t iters, double* ms_a, double* ms_b, double* ms_f) {
-    if (!h || iters < 1) return invalid("bad arguments");
-    cudaEvent_t ev[4];
-    for (auto& e : ev) FW_CUDA(cudaEventCreate(&e));
-    double ta = 0.0, tb = 0.0, tf = 0.0;
-    int done = 0;
+    if (!h || iters < 1 || iters > 4096) return invalid("bad arguments (iters in [1, 4096])");
+    // all iterations are enqueued back to back with an event between
+    // consecutive kernels, and the host waits once at the end, so each interval
+    // is the kernel's time in a busy stream (no per-launch idle gap)
+    std::vector<cudaEvent_t> ev(3 * size_t(iters) + 1, nullptr);
     fw_status rc = FW_OK;
-    for (int i = 0; i < iters; ++i) {
-        cudaEventRecord(ev[0], h->stream);
-        h->ops->passA(h->pd, h->st, h->stream);
-        cudaEventRecord(ev[1], h->stream);
-        h->ops->passB(h->pd, h->st, h->stream);
-        cudaEventRecord(ev[2], h->stream);
-        h->ops->finish(h->pd, h->st, h->stream);
-        cudaEventRecord(ev[3], h->stream);
-        cudaError_t e = cudaEventSynchronize(ev[3]);
-        if (e != cudaSuccess) {
-            rc = cuda_fail(e, "profile iteration");
+    for (auto& e : ev) {
+        const cudaError_t ce = cudaEventCreate(&e);
+        if (ce != cudaSuccess) {
+            rc = cuda_fail(ce, "cudaEventCreate");
             break;
         }
-        float a = 0.f, b = 0.f, f = 0.f;
-        cudaEventElapsedTime(&a, ev[0], ev[1]);
-        cudaEventElapsedTime(&b, ev[1], ev[2]);
-        cudaEventElapsedTime(&f, ev[2], ev[3]);
-        ta += a;
-        tb += b;
-        tf += f;
-        ++done;
     }
-    for (auto& e : ev) cudaEventDestroy(e);
+    if (rc == FW_OK) {
+        for (int i = 0; i < iters; ++i) {
+            cudaEventRecord(ev[3 * i], h->stream);
+            h->ops->passA(h->pd, h->st, h->stream);
+            cudaEventRecord(ev[3 * i + 1], h->stream);
+            h->ops->passB(h->pd, h->st, h->stream);
+            cudaEventRecord(ev[3 * i + 2], h->stream);
+            h->ops->finish(h->pd, h->st, h->stream);
+        }
+        cudaEventRecord(ev[3 * size_t(iters)], h->stream);
+        const cudaError_t ce = cudaEventSynchronize(ev[3 * size_t(iters)]);
+        if (ce != cudaSuccess) rc = cuda_fail(ce, "profile iterations");
+    }
+    double ta = 0.0, tb = 0.0, tf = 0.0;
+    if (rc == FW_OK) {
+        for (int i = 0; i < iters; ++i) {
+            float a = 0.f, b = 0.f, f = 0.f;
+            cudaEventElapsedTime(&a, ev[3 * i], ev[3 * i + 1]);
+            cudaEventElapsedTime(&b, ev[3 * i + 1], ev[3 * i + 2]);
+            cudaEventElapsedTime(&f, ev[3 * i + 2], ev[3 * i + 3]);
+            ta += a;
+            tb += b;
+            tf += f;
+        }
+    }
+    for (auto& e : ev)
+        if (e) cudaEventDestroy(e);
     if (rc != FW_OK) return rc;
-    if (ms_a) *ms_a = ta / done;
-    if (ms_b) *ms_b = tb / done;
-    if (ms_f) *ms_f = tf / done;
+    if (ms_a) *ms_a = ta / iters;
+    if (ms_b) *ms_b = tb / iters;
+    if (ms_f) *ms_f = tf / iters;
     return flush(h);
 }
 

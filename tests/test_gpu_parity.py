@@ -210,6 +210,20 @@ def test_oneshot_sbm200k_vs_oracle():
     assert agreement(lab, s_o) >= 0.999
 
 
+# ---------------------------------------------------------- profile --
+
+def test_profile_times_and_advances_like_step(blobs2k):
+    """fw_seg_profile runs ordinary iterations: positive per-kernel times, and
+    the iterate afterwards is bitwise the one step() reaches."""
+    with B.Segmenter(blobs2k, weight_dtype="f32", max_iters=10 ** 6) as a, \
+            B.Segmenter(blobs2k, weight_dtype="f32", max_iters=10 ** 6) as b:
+        ms_a, ms_b, ms_f = a.profile(7)
+        assert ms_a > 0 and ms_b > 0 and ms_f > 0
+        b.step(7)
+        assert np.array_equal(a.U(), b.U())
+        assert a.stats().iters == b.stats().iters == 7
+
+
 # ---------------------------------------------------------- LMO gap --
 
 @pytest.mark.parametrize("weights,tol", [("f64", 1e-9), ("f32", TOL)])
