@@ -74,8 +74,11 @@ __device__ __forceinline__ int grid_sync(GridBar* bar, long long budget, int nli
     return s_r;
 }
 
+// Held to 48 registers for the FP32 iterate so that 5 blocks per SM stay
+// resident; pass A stages one 256-row sub-tile at a time (a batch item is
+// usually a single sub-tile, so a second buffer would only cost residency).
 template <typename T, typename WT, int KMAX>
-__global__ void __launch_bounds__(kBlock) k_persistent(BatchArgs a) {
+__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 5 : 2) k_persistent(BatchArgs a) {
     extern __shared__ __align__(128) unsigned char smraw[];
     T* sm_lane = reinterpret_cast<T*>(smraw);
     T* sm_row = sm_lane + kBlock * (KMAX | 1);
@@ -113,9 +116,8 @@ __global__ void __launch_bounds__(kBlock) k_persistent(BatchArgs a) {
                     const int2 wk = a.work[ww];
                     ProbState* st = a.state + wk.x;
                     if (phase == 0)
-                        tile_A<T, KMAX>(s_pd, st, wk.y, s_upd != 0, s_alpha, stage,
-                                        s_pd.tile_rows > kBlock ? max_stages<T, KMAX>() : 1,
-                                        bars, mb_phases);
+                        tile_A<T, KMAX>(s_pd, st, wk.y, s_upd != 0, s_alpha, stage, 1, bars,
+                                        mb_phases);
                     else
                         tile_B<T, WT, KMAX, false, true>(s_pd, st, wk.y, sm_lane, sm_row,
                                                          &a.bar->ndone);
@@ -147,7 +149,7 @@ class BatchKernImpl final : public BatchKern {
 public:
     size_t smem() const override {
         const size_t b = 2 * size_t(kBlock) * (KMAX | 1) * sizeof(T);
-        const size_t a = max_stages<T, KMAX>() * 3 * size_t(kBlock) * KMAX * sizeof(T);
+        const size_t a = 3 * size_t(kBlock) * KMAX * sizeof(T);   // one staging buffer
         const size_t r = size_t(kBlock) * kNumR * sizeof(double);
         const size_t m = a > b ? a : b;
         return m > r ? m : r;
