@@ -83,9 +83,11 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 5 : 2) k_persistent(B
     T* sm_lane = reinterpret_cast<T*>(smraw);
     T* sm_row = sm_lane + kBlock * (KMAX | 1);
     T* stage = reinterpret_cast<T*>(smraw);        // phases A and B use the buffer in turn
-    __shared__ ProbDesc s_pd;
-    __shared__ int s_w, s_skip, s_upd;
-    __shared__ T s_alpha;
+    // two item slots: warp 1 fetches the next (problem, tile) item, its
+    // descriptor and its scalars while the block works on the current one
+    __shared__ ProbDesc s_pd[2];
+    __shared__ int s_w[2], s_skip[2], s_upd[2];
+    __shared__ T s_alpha[2];
     __shared__ __align__(8) uint64_t bars[2];
     if (threadIdx.x == 0) {
         mbar_init(&bars[0], 1);
@@ -95,34 +97,39 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 5 : 2) k_persistent(B
     uint32_t mb_phases = 0;   // parities of the two bulk-copy mbarriers
     for (int it = 0; it < a.iters; ++it) {
         for (int phase = 0; phase < 2; ++phase) {
-            int w = blockIdx.x;
-            for (;;) {
-                if (threadIdx.x == 0) {
-                    const int ww = a.dynamic ? int(atomicAdd(&a.bar->ctr[phase], 1u)) : w;
-                    s_w = ww;
-                    if (ww < a.nwork) {
-                        const int2 wk = a.work[ww];
-                        s_pd = a.desc[wk.x];
-                        const ProbState* st = a.state + wk.x;
-                        s_skip = ld_cg(&st->done);
-                        s_upd = ld_cg(&st->has_update);
-                        s_alpha = alpha_of<T>(st);
-                    }
+            // one thread fills slot `sl` with the item after `w` in this block's order
+            auto fetch = [&](int sl, int w) {
+                const int ww = a.dynamic ? int(atomicAdd(&a.bar->ctr[phase], 1u)) : w;
+                s_w[sl] = ww;
+                if (ww < a.nwork) {
+                    const int2 wk = a.work[ww];
+                    s_pd[sl] = a.desc[wk.x];
+                    const ProbState* st = a.state + wk.x;
+                    s_skip[sl] = ld_cg(&st->done);
+                    s_upd[sl] = ld_cg(&st->has_update);
+                    s_alpha[sl] = alpha_of<T>(st);
                 }
-                __syncthreads();
-                const int ww = s_w;
+            };
+            int w = blockIdx.x;
+            int c = 0;
+            if (threadIdx.x == 32) fetch(0, w);
+            __syncthreads();
+            for (;;) {
+                const int ww = s_w[c];
                 if (ww >= a.nwork) break;
-                if (!s_skip) {
+                if (threadIdx.x == 32) fetch(c ^ 1, w + int(gridDim.x));
+                if (!s_skip[c]) {
                     const int2 wk = a.work[ww];
                     ProbState* st = a.state + wk.x;
                     if (phase == 0)
-                        tile_A<T, KMAX>(s_pd, st, wk.y, s_upd != 0, s_alpha, stage, 1, bars,
-                                        mb_phases);
+                        tile_A<T, KMAX>(s_pd[c], st, wk.y, s_upd[c] != 0, s_alpha[c], stage, 1,
+                                        bars, mb_phases);
                     else
-                        tile_B<T, WT, KMAX, false, true>(s_pd, st, wk.y, sm_lane, sm_row,
+                        tile_B<T, WT, KMAX, false, true>(s_pd[c], st, wk.y, sm_lane, sm_row,
                                                          &a.bar->ndone);
                 }
-                __syncthreads();
+                __syncthreads();   // the prefetched slot is complete, the current one free
+                c ^= 1;
                 w += gridDim.x;
             }
             const int r = grid_sync(a.bar, a.budget, a.nlive, a.expect_extra);
