@@ -78,7 +78,6 @@ struct HostGraph {
 struct ProbLayout {
     int64_t n = 0, nnz = 0, nnz_pad = 0, npad = 0;
     int32_t K = 0, tile_rows = 0, ntiles = 0, lanes = 1;
-    std::vector<int32_t> rpp;   // padded row_ptr (local offsets)
 };
 
 // Host checks (options, row_ptr, labels) and the padded layout.

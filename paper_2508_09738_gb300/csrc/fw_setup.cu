@@ -66,6 +66,95 @@ __global__ void __launch_bounds__(kBlock) k_state_init(ProbState* st, const doub
     }
 }
 
+// Padded row offsets (every row rounded up to kPadW entries), an exclusive
+// scan over the rows in three steps: per 1024-row block, over the block
+// totals (one block), then the block offsets added back.  Integer, so exact.
+constexpr int kScanRows = 4 * kBlock;
+
+__global__ void __launch_bounds__(kBlock)
+k_pad_scan_local(int64_t n, const int32_t* __restrict__ rp, int32_t* __restrict__ out,
+                 int32_t* __restrict__ bsum) {
+    __shared__ int32_t wsum[kBlock / 32];
+    const int64_t base = blockIdx.x * int64_t(kScanRows) + threadIdx.x * 4;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t v[4];
+    int32_t s = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int64_t i = base + q;
+        const int32_t d = i < n ? rp[i + 1] - rp[i] : 0;
+        v[q] = (d + (kPadW - 1)) & ~(kPadW - 1);
+        s += v[q];
+    }
+    int32_t x = s;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, x, off);
+        if (lane >= off) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int32_t run = 0;
+        for (int w = 0; w < kBlock / 32; ++w) {
+            const int32_t t = wsum[w];
+            wsum[w] = run;
+            run += t;
+        }
+        bsum[blockIdx.x] = run;
+    }
+    __syncthreads();
+    int32_t excl = x - s + wsum[warp];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int64_t i = base + q;
+        if (i < n) out[i] = excl;
+        excl += v[q];
+    }
+}
+
+// Exclusive scan of the nb block totals in place (one block); total -> out[n].
+__global__ void __launch_bounds__(kBlock)
+k_pad_scan_blocks(int64_t n, int nb, int32_t* __restrict__ bsum, int32_t* __restrict__ out) {
+    __shared__ int32_t wsum[kBlock / 32];
+    __shared__ int32_t carry;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int b0 = 0; b0 < nb; b0 += kBlock) {
+        const int b = b0 + threadIdx.x;
+        const int32_t s = b < nb ? bsum[b] : 0;
+        int32_t x = s;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, x, off);
+            if (lane >= off) x += y;
+        }
+        if (lane == 31) wsum[warp] = x;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int32_t run = 0;
+            for (int w = 0; w < kBlock / 32; ++w) {
+                const int32_t t = wsum[w];
+                wsum[w] = run;
+                run += t;
+            }
+        }
+        __syncthreads();
+        const int32_t c = carry;
+        if (b < nb) bsum[b] = c + x - s + wsum[warp];
+        __syncthreads();
+        if (threadIdx.x == kBlock - 1) carry = c + x + wsum[warp];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[n] = carry;
+}
+
+__global__ void k_pad_scan_add(int64_t n, const int32_t* __restrict__ bsum, int32_t* out) {
+    const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (i < n) out[i] += bsum[i / kScanRows];
+}
+
 __global__ void k_fid(int64_t n, const int32_t* labels, int8_t* fid) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n) fid[i] = int8_t(labels[i]);
@@ -147,23 +236,27 @@ fw_status plan_problem(const HostGraph& g, const fw_seg_opts& o, ProbLayout& lay
         return FW_ERR_GRAPH;
     }
     const int64_t n = g.n;
-    lay.rpp.assign(size_t(n) + 1, 0);
-    int64_t acc = 0;
+    // one branch-free pass each (the padded row offsets themselves are formed
+    // on the device): a negative row length sets the sign bit of `neg`
+    int64_t acc = 0, neg = 0;
+    const int32_t* __restrict__ rp = g.rp;
     for (int64_t i = 0; i < n; ++i) {
-        const int64_t d = int64_t(g.rp[i + 1]) - g.rp[i];
-        if (d < 0) {
-            set_error("row_ptr must be non-decreasing");
-            return FW_ERR_GRAPH;
-        }
-        acc += round_up(d, kPadW);
-        if (acc >= (int64_t(1) << 31)) {
-            set_error("padded nnz must stay below 2^31");
-            return FW_ERR_UNSUPPORTED;
-        }
-        lay.rpp[size_t(i) + 1] = int32_t(acc);
+        const int64_t d = int64_t(rp[i + 1]) - int64_t(rp[i]);
+        neg |= d;
+        acc += (d + (kPadW - 1)) & ~int64_t(kPadW - 1);
     }
-    for (int64_t i = 0; i < n; ++i)
-        if (g.labels[i] < -1 || g.labels[i] >= g.K) return invalid("labels must be -1 or in [0, K)");
+    if (neg < 0) {
+        set_error("row_ptr must be non-decreasing");
+        return FW_ERR_GRAPH;
+    }
+    if (acc >= (int64_t(1) << 31)) {
+        set_error("padded nnz must stay below 2^31");
+        return FW_ERR_UNSUPPORTED;
+    }
+    int bad = 0;
+    const int32_t* __restrict__ lab = g.labels;
+    for (int64_t i = 0; i < n; ++i) bad |= int(lab[i] < -1) | int(lab[i] >= g.K);
+    if (bad) return invalid("labels must be -1 or in [0, K)");
     lay.n = n;
     lay.nnz = g.rp[n];
     lay.nnz_pad = acc;
@@ -296,8 +389,16 @@ fw_status assemble_problem(Ops* ops, const HostGraph& g, const ProbLayout& lay, 
         FW_CUDA(cudaMemcpyAsync(d_w, g.w, 8 * size_t(nnz), cudaMemcpyHostToDevice, s));
     }
     FW_CUDA(cudaMemcpyAsync(d_lab, g.labels, 4 * size_t(n), cudaMemcpyHostToDevice, s));
-    FW_CUDA(cudaMemcpyAsync(const_cast<int32_t*>(pd.rp), lay.rpp.data(), 4 * (size_t(n) + 1),
-                            cudaMemcpyHostToDevice, s));
+    {   // padded row offsets into pd.rp
+        const int nb = int((n + kScanRows - 1) / kScanRows);
+        int32_t* d_bsum = nullptr;
+        FW_TRYS(t.get(&d_bsum, 4 * size_t(nb)));
+        int32_t* prp = const_cast<int32_t*>(pd.rp);
+        k_pad_scan_local<<<nb, kBlock, 0, s>>>(n, d_rp, prp, d_bsum);
+        k_pad_scan_blocks<<<1, kBlock, 0, s>>>(n, nb, d_bsum, prp);
+        k_pad_scan_add<<<unsigned((n + kBlock - 1) / kBlock), kBlock, 0, s>>>(n, d_bsum, prp);
+        FW_TRYS(launched("row offset scan"));
+    }
     const size_t blk = te * size_t(lay.npad) * size_t(lay.K);
     FW_CUDA(cudaMemsetAsync(pd.U, 0, blk, s));
     FW_CUDA(cudaMemsetAsync(pd.LS, 0, blk, s));
