@@ -7,6 +7,8 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <system_error>
+#include <thread>
 #include <vector>
 
 #include "fw_device.cuh"
@@ -236,14 +238,54 @@ fw_status plan_problem(const HostGraph& g, const fw_seg_opts& o, ProbLayout& lay
         return FW_ERR_GRAPH;
     }
     const int64_t n = g.n;
-    // one branch-free pass each (the padded row offsets themselves are formed
-    // on the device): a negative row length sets the sign bit of `neg`
+    // branch-free passes over row_ptr and labels (the padded row offsets
+    // themselves are formed on the device): a negative row length sets the
+    // sign bit of `neg`.  Large inputs are split over a few host threads.
+    struct Part {
+        int64_t acc = 0, neg = 0;
+        int bad = 0;
+    };
+    auto scan_part = [&g](int64_t i0, int64_t i1, Part& p) {
+        const int32_t* __restrict__ rp = g.rp;
+        const int32_t* __restrict__ lab = g.labels;
+        int64_t acc = 0, neg = 0;
+        int bad = 0;
+        for (int64_t i = i0; i < i1; ++i) {
+            const int64_t d = int64_t(rp[i + 1]) - int64_t(rp[i]);
+            neg |= d;
+            acc += (d + (kPadW - 1)) & ~int64_t(kPadW - 1);
+            bad |= int(lab[i] < -1) | int(lab[i] >= g.K);
+        }
+        p.acc = acc;
+        p.neg = neg;
+        p.bad = bad;
+    };
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const int nt = n >= (int64_t(1) << 20) ? int(std::min(8u, hw)) : 1;
+    std::vector<Part> parts(static_cast<size_t>(nt));
+    bool threaded = false;
+    if (nt > 1) {
+        std::vector<std::thread> th;
+        try {
+            for (int t = 0; t < nt; ++t)
+                th.emplace_back(scan_part, n * t / nt, n * (t + 1) / nt,
+                                std::ref(parts[size_t(t)]));
+            threaded = true;
+        } catch (const std::system_error&) {
+            threaded = false;   // no threads available: one pass below
+        }
+        for (auto& x : th) x.join();
+    }
+    if (!threaded) {
+        parts.assign(1, Part());
+        scan_part(0, n, parts[0]);
+    }
     int64_t acc = 0, neg = 0;
-    const int32_t* __restrict__ rp = g.rp;
-    for (int64_t i = 0; i < n; ++i) {
-        const int64_t d = int64_t(rp[i + 1]) - int64_t(rp[i]);
-        neg |= d;
-        acc += (d + (kPadW - 1)) & ~int64_t(kPadW - 1);
+    int bad = 0;
+    for (const Part& p : parts) {
+        acc += p.acc;
+        neg |= p.neg;
+        bad |= p.bad;
     }
     if (neg < 0) {
         set_error("row_ptr must be non-decreasing");
@@ -253,9 +295,6 @@ fw_status plan_problem(const HostGraph& g, const fw_seg_opts& o, ProbLayout& lay
         set_error("padded nnz must stay below 2^31");
         return FW_ERR_UNSUPPORTED;
     }
-    int bad = 0;
-    const int32_t* __restrict__ lab = g.labels;
-    for (int64_t i = 0; i < n; ++i) bad |= int(lab[i] < -1) | int(lab[i] >= g.K);
     if (bad) return invalid("labels must be -1 or in [0, K)");
     lay.n = n;
     lay.nnz = g.rp[n];
