@@ -226,7 +226,7 @@ def run_batched(args, rank, world, local):
     weights = args.weights or "bf16"
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    opts = B.fw_seg_default_opts(max_iters=iters, weight_dtype=weights)
+    opts = B.fw_seg_default_opts(max_iters=iters, weight_dtype=weights, lanes_per_row=args.lanes)
     cache = os.environ.get("FW_TUNE_CACHE") or os.path.join(tempfile.gettempdir(), "fwseg_tune.txt")
     t0 = time.time()
     bt = B.Batch(gs, opts, weight_dtype=weights, cuda_stream=stream.cuda_stream, tune_cache=cache)

@@ -122,11 +122,12 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 5 : 2) k_persistent(B
                     const int2 wk = a.work[ww];
                     ProbState* st = a.state + wk.x;
                     if (phase == 0)
-                        tile_A<T, KMAX>(s_pd[c], st, wk.y, s_upd[c] != 0, s_alpha[c], stage, 1,
+                        tile_A<T, KMAX>(s_pd[c], st, wk.y, s_upd[c] != 0, s_alpha[c],
+                                        FuseCtl{false, nullptr, nullptr}, s_pd[c].acc, stage, 1,
                                         bars, mb_phases);
                     else
                         tile_B<T, WT, KMAX, false, true>(s_pd[c], st, wk.y, sm_lane, sm_row,
-                                                         &a.bar->ndone);
+                                                         s_pd[c].acc, &a.bar->ndone);
                 }
                 __syncthreads();   // the prefetched slot is complete, the current one free
                 c ^= 1;

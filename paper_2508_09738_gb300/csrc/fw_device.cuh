@@ -8,9 +8,12 @@
 //                       the greedy LMO choice (eq. eq:LMOpr) and the per-row pieces of
 //                       the FW gap g = -<G, D> and of ||D||^2, sum w_i ||D_i||^2, <D, LU>.
 //   pass B (CSR pass):  LS = L S for the one-hot S: (L S)_ik = [s_i = k] - sum_{j: s_j = k} W^_ij,
-//                       and the per-row <D_i, LS_i>; the last block forms
-//                       q = <D, L D> + sum w_i||D_i||^2 - (2/eps)||D||^2  (Hessian of App. C)
-//                       and the exact step a = min(1, g/q) (1 if q <= 0).
+//                       and the per-row <D_i, LS_i>.
+// Both passes add block totals into exact fixed-point accumulators; from the
+// totals one warp (warp_decide) forms q = <D, L D> + sum w_i||D_i||^2 -
+// (2/eps)||D||^2 (Hessian of App. C), runs the stop test and takes the exact
+// step a = min(1, g/q) (1 if q <= 0), either in k_finish or at the start of
+// the next pass A.
 // L U is never recomputed inside the loop: it follows the recurrence above, and a
 // separate SpMM (spmm_rows) builds it at the start and on refresh.
 #pragma once
@@ -428,6 +431,7 @@ template <typename T, int KMAX, int MODE>
 __device__ __forceinline__ void passA_rows(const ProbDesc& pd, int r_begin, int r_end, bool upd,
                                            T alpha, AccA<T>& acc, T* __restrict__ Gout,
                                            uint8_t* __restrict__ chout) {
+    static_assert(MODE != MODE_STEP, "the step pass is passA_staged (it keeps cls4 current)");
     const int K = pd.K;
     const int64_t np = pd.npad;
     T* __restrict__ Ub = static_cast<T*>(pd.U);
@@ -488,6 +492,141 @@ __device__ __forceinline__ void passA_rows(const ProbDesc& pd, int r_begin, int 
     }
 }
 
+// ------------------------------------------------------------ scalar steps
+// The problem's constants of the stop test and step rule.
+struct StepCfg {
+    double inv_eps, gap_tol;
+    int tol_mode, max_iters, step_rule;
+};
+
+__device__ __forceinline__ StepCfg step_cfg(const ProbDesc& pd) {
+    return StepCfg{pd.inv_eps, pd.gap_tol, pd.tol_mode, pd.max_iters, pd.step_rule};
+}
+
+static_assert(kAccCopies == 1, "warp_decide reads one accumulator copy");
+
+// The step decision of one iteration, taken by one warp (all 32 lanes call
+// it) from the iteration's totals S = (g, ||D||^2, sum w||D||^2, <D,LU>, |I|,
+// <D,LS>) in accumulator bank `accb` and the inputs in[c]: the stop test of
+// Alg. 3 step 4, then the curvature q = <D, H D> and the step (exact line
+// search, eq. 10, or Armijo halving).
+//
+// Lane l loads word l of the bank; lanes 16..19 load in[c] and the error
+// flag, so everything arrives in one round trip, and lane 2q turns quantity
+// q into a double.  Spread this way the decision needs few registers per
+// thread, which matters where it is fused into pass A.  With `commit` the
+// warp writes the result into the state (each statistic from its lane, the
+// rest from lane 0), in[c ^ 1] included; q and alpha keep their last values
+// once done.  k_finish, pass A (fused) and the persistent kernel's last block
+// all run this code, so their decisions agree bit for bit.
+// Returns `done` in every lane; *alpha = the step.
+__device__ __forceinline__ int warp_decide(const unsigned long long* accb, ProbState* st, int c,
+                                           const StepCfg& cfg, bool commit, double* alpha) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned long long* inw = reinterpret_cast<const unsigned long long*>(&st->in[c]);
+    unsigned long long w = 0ull;
+    if (lane < kAccWords) w = __ldcg(accb + lane);
+    else if (lane >= 16 && lane < 19) w = __ldcg(inw + (lane - 16));
+    else if (lane == 19) w = static_cast<unsigned long long>(static_cast<unsigned>(__ldcg(&st->err)));
+    // Q64.64 (lo word in lane 2q, hi in 2q+1) -> double
+    const unsigned long long hw = __shfl_down_sync(full, w, 1);
+    double Sq = double(static_cast<long long>(hw)) + ldexp(double(w), -64);
+    if (__shfl_sync(full, w, kAccFlag) != 0ull && lane == 0) Sq = CUDART_NAN;
+    const bool bad = (lane == 0 || lane == 2 || lane == 4 || lane == 6 || lane == 10) && !isfinite(Sq);
+    const bool nonfinite = __any_sync(full, bad);
+    const double g = __shfl_sync(full, Sq, 0);
+    const int active = int(__shfl_sync(full, Sq, 8));
+    const double qL = __shfl_sync(full, Sq, 10) - __shfl_sync(full, Sq, 6);   // <D, L D>
+    const double q =
+        qL + __shfl_sync(full, Sq, 4) - 2.0 * cfg.inv_eps * __shfl_sync(full, Sq, 2);  // <D, H D>
+    const double E = __longlong_as_double(static_cast<long long>(__shfl_sync(full, w, 16)));
+    const double g0in = __longlong_as_double(static_cast<long long>(__shfl_sync(full, w, 17)));
+    const unsigned long long ig = __shfl_sync(full, w, 18);
+    const int iter = int(static_cast<unsigned>(ig));
+    const int g0_set = int(static_cast<unsigned>(ig >> 32));
+    const int err = int(__shfl_sync(full, w, 19));
+    const double g0 = g0_set ? g0in : g;
+    int status = 2;  // FW_PENDING
+    int done = 0;
+    if (err) {
+        status = -7;  // FW_ERR_TIMEOUT
+        done = 1;
+    } else if (nonfinite) {
+        status = -6;  // FW_ERR_NUMERIC
+        done = 1;
+    } else if (active == 0 || g <= 0.0) {
+        status = 0;
+        done = 1;
+    } else if (g <= (cfg.tol_mode ? cfg.gap_tol * g0 : cfg.gap_tol)) {
+        status = 0;
+        done = 1;
+    } else if (iter >= cfg.max_iters) {
+        status = 1;  // FW_NOT_CONVERGED
+        done = 1;
+    } else if (!isfinite(q)) {
+        status = -6;
+        done = 1;
+    }
+    double a = 1.0;
+    if (!done && q > 0.0) {
+        const double r = g / q;   // one division serves both rules
+        if (cfg.step_rule == 0) {
+            a = fmin(1.0, r);
+        } else {
+            // Armijo: largest 0.5^j with E(U) - E(U + a D) = a g - a^2 q / 2 >= 1e-6 a g,
+            // i.e. a <= 2 (1 - 1e-6) g / q
+            const double amax = 2.0 * (1.0 - 1e-6) * r;
+            for (int j = 0; j < 1100 && a > amax; ++j) a *= 0.5;
+        }
+    }
+    if (commit) {
+        if (lane == 0) st->g = Sq;
+        if (lane == 2) st->nD = Sq;
+        if (lane == 4) st->nW = Sq;
+        if (lane == 6) st->tLU = Sq;
+        if (lane == 8) st->active = int(Sq);
+        if (lane == 10) st->pLS = Sq;
+        if (lane == 0) {
+            st->g0 = g0;
+            st->g0_set = 1;
+            st->status = status;
+            st->done = done;
+            StepIn nx;
+            nx.E = E;
+            nx.g0 = g0;
+            nx.iter = iter;
+            nx.g0_set = 1;
+            if (!done) {
+                st->q = q;
+                st->alpha = a;
+                st->alpha_f = float(a);
+                nx.E = E - a * g + 0.5 * a * a * q;
+                nx.iter = iter + 1;
+            }
+            st->has_update = done ? 0 : 1;
+            st->E = nx.E;
+            st->iter = nx.iter;
+            st->in[c ^ 1] = nx;
+        }
+    }
+    *alpha = a;
+    return done;
+}
+
+// k_finish and the persistent kernel's last block: one warp decides on bank
+// `accb` (the totals of the iteration that just ended), clears it, commits,
+// and advances the parity.  Returns done.
+__device__ __forceinline__ int warp_finish(const ProbDesc& pd, ProbState* st,
+                                           unsigned long long* accb) {
+    const int c = __ldcg(&st->cur);
+    double a;
+    const int done = warp_decide(accb, st, c, step_cfg(pd), true, &a);
+    if ((threadIdx.x & 31) < kAccWords) accb[threadIdx.x & 31] = 0ull;   // after its own load
+    if ((threadIdx.x & 31) == 0) st->cur = c ^ 1;
+    return done;
+}
+
 // Staged pass A over rows [r_begin, r_end) in 256-row sub-tiles.  For each
 // sub-tile one thread issues bulk copies of its class columns of U, LU (and LS
 // when a step is pending) into a stage buffer (T[3][KMAX][256]) completing on
@@ -524,23 +663,40 @@ __device__ __forceinline__ void stage_issue(const ProbDesc& pd, int base, int ro
     }
 }
 
+// Pass A with the previous iteration's step decision fused in (ProbState):
+// when `fin`, the block decides on accumulator bank `cur` and in[cur] while
+// its first copies are in flight, and block 0 (`commit`) writes the result.
+struct FuseCtl {
+    bool fin;
+    const int* stop;        // shared memory: the decision stops the solve
+    const double* alpha;    // shared memory: the decided step
+};
+
+// Outcomes of passA_staged.
+enum { kPassOk = 0, kPassTimeout = 1, kPassStopped = 2 };
+
 // EXACT: the problem has exactly KMAX classes, so every per-class guard of
-// the unrolled loops is known at compile time.
+// the unrolled loops is known at compile time.  With fc.fin, `upd` must be
+// true and `alpha` is replaced by the decided step; if the decision stops the
+// solve, the block waits for its copies and returns kPassStopped without
+// touching the iterate.
 template <typename T, int KMAX, bool EXACT = false>
-__device__ __forceinline__ bool passA_staged(const ProbDesc& pd, int r_begin, int r_end, bool upd,
-                                             T alpha, AccA<T>& acc, T* stage, int nstages,
-                                             uint64_t* bars, uint32_t& phases) {
+__device__ __forceinline__ int passA_staged(const ProbDesc& pd, int r_begin, int r_end, bool upd,
+                                            T alpha, const FuseCtl& fc, AccA<T>& acc, T* stage,
+                                            int nstages, uint64_t* bars, uint32_t& phases) {
     const int K = EXACT ? KMAX : pd.K;
     const int64_t np = pd.npad;
     T* __restrict__ Ub = static_cast<T*>(pd.U);
     T* __restrict__ LUb = static_cast<T*>(pd.LU);
     const T c2 = c2_of<T>(pd);
     const T om = om_of<T>(pd);
-    const T oma = sub_(T(1), alpha);
+    T oma = sub_(T(1), alpha);
     const bool greedy = pd.oracle == 0;
     const int stage_elems = 3 * KMAX * kBlock;
-    bool ok = true;
-    if (threadIdx.x == 0 && r_begin < r_end)
+    int rc = kPassOk;
+    // with fc.fin the caller has issued the first sub-tile's copies and taken
+    // the decision (s_stop, s_alpha) before calling
+    if (!fc.fin && threadIdx.x == 0 && r_begin < r_end)
         stage_issue<T, KMAX>(pd, r_begin, min(kBlock, r_end - r_begin), upd, stage, &bars[0]);
     int j = 0;
     for (int base = r_begin; base < r_end; base += kBlock, ++j) {
@@ -558,6 +714,7 @@ __device__ __forceinline__ bool passA_staged(const ProbDesc& pd, int r_begin, in
         // per-row bytes are loaded before the wait so their latency overlaps the copies
         const uint8_t sv = (t < rows && upd) ? ld_cg(pd.choice + r) : uint8_t(0);
         const int f = t < rows ? int(__ldg(pd.fid + r)) : -1;
+        int my_cls = 0;
         if (nstages > 1 && threadIdx.x == 0 && base + kBlock < r_end) {
             const int nb = base + kBlock;   // prefetch the next sub-tile into the other buffer
             stage_issue<T, KMAX>(pd, nb, min(kBlock, r_end - nb), upd,
@@ -569,7 +726,7 @@ __device__ __forceinline__ bool passA_staged(const ProbDesc& pd, int r_begin, in
             // a copy did not arrive in time: wait (bounded) for the copies still
             // in flight into this block's buffers, then leave the tile; the
             // caller raises the problem's error flag
-            ok = false;
+            rc = kPassTimeout;
             if (got || mbar_wait(&bars[buf], par)) phases ^= 1u << buf;
             if (nstages > 1 && base + kBlock < r_end &&
                 mbar_wait(&bars[buf ^ 1], (phases >> (buf ^ 1)) & 1u))
@@ -578,6 +735,16 @@ __device__ __forceinline__ bool passA_staged(const ProbDesc& pd, int r_begin, in
             break;
         }
         phases ^= 1u << buf;
+        if (fc.fin && j == 0) {
+            if (*fc.stop) {   // stopped: nothing is applied; let the prefetch land
+                if (nstages > 1 && base + kBlock < r_end &&
+                    mbar_wait(&bars[buf ^ 1], (phases >> (buf ^ 1)) & 1u))
+                    phases ^= 1u << (buf ^ 1);
+                return kPassStopped;
+            }
+            alpha = T(*fc.alpha);
+            oma = sub_(T(1), alpha);
+        }
         if (t < rows) {
             const int sp = sv & 0x7f;
             const bool mv = (sv & kActiveBit) != 0;
@@ -645,10 +812,15 @@ __device__ __forceinline__ bool passA_staged(const ProbDesc& pd, int r_begin, in
             acc.tLU = add_(acc.tLU, tLU);
             acc.act = add_(acc.act, moved ? T(1) : T(0));
             pd.choice[r] = uint8_t(s) | (moved ? kActiveBit : uint8_t(0));
+            my_cls = s;
+        }
+        if (pd.cls4) {   // rows 2m, 2m+1 are adjacent lanes (base is a multiple of 256)
+            const int hi = __shfl_down_sync(0xffffffffu, my_cls, 1);
+            if ((t & 1) == 0 && t < rows) pd.cls4[r >> 1] = uint8_t(my_cls | (hi << 4));
         }
         __syncthreads();
     }
-    return ok;
+    return rc;
 }
 
 // Stage 1 of the sparse passes: for each row of a 256-row sub-tile, `L` lanes
@@ -758,8 +930,23 @@ __device__ __forceinline__ void csr_bins(const ProbDesc& pd, const T* __restrict
                 const int nt = two ? 8 : 4;
                 if (ONEHOT) {
                     int sj[8];
+                    if constexpr (KMAX <= 16 && RO) {
+                        // 4-bit classes: half the gathered footprint, so more of it
+                        // stays in L1.  Only the two-kernel path (RO) keeps them;
+                        // the persistent kernel gathers the class bytes.
+                        // the nibble selectors of the 8 gathers share one register
+                        uint32_t odd = 0;
 #pragma unroll
-                    for (int t = 0; t < 8; ++t) sj[t] = ld_gather<RO>(choice + cc[t]) & 0x7f;
+                        for (int t = 0; t < 8; ++t) {
+                            sj[t] = ld_gather<RO>(pd.cls4 + (cc[t] >> 1));
+                            odd |= uint32_t(cc[t] & 1) << (2 + 4 * t);
+                        }
+#pragma unroll
+                        for (int t = 0; t < 8; ++t) sj[t] = (sj[t] >> ((odd >> 4 * t) & 4)) & 15;
+                    } else {
+#pragma unroll
+                        for (int t = 0; t < 8; ++t) sj[t] = ld_gather<RO>(choice + cc[t]) & 0x7f;
+                    }
 #pragma unroll
                     for (int t = 0; t < 8; ++t)
                         if (t < nt) my[sj[t]] = add_(my[sj[t]], v[t]);
@@ -941,126 +1128,45 @@ __device__ __forceinline__ void osfw_rows(const ProbDesc& pd, int32_t* __restric
     }
 }
 
-// ------------------------------------------------------------ scalar steps
-// Run by one thread of the last block of pass B with the problem totals
-// S = (g, ||D||^2, sum w||D||^2, <D,LU>, |I|, <D,LS>) of this iteration:
-// the stop test of Alg. 3 step 4, then the curvature and the step.
-__device__ __forceinline__ void finish_iter(const ProbDesc& pd, ProbState* st,
-                                            const double (&S)[kNumR]) {
-    st->g = S[0];
-    st->nD = S[1];
-    st->nW = S[2];
-    st->tLU = S[3];
-    st->active = int(S[4]);
-    st->pLS = S[5];
-    if (!st->g0_set) {
-        st->g0 = S[0];
-        st->g0_set = 1;
-    }
-    st->has_update = 0;
-    int status = 2;  // FW_PENDING
-    int done = 0;
-    if (__ldcg(&st->err)) {
-        status = -7;  // FW_ERR_TIMEOUT
-        done = 1;
-    } else if (!isfinite(S[0]) || !isfinite(S[1]) || !isfinite(S[2]) || !isfinite(S[3]) ||
-               !isfinite(S[5])) {
-        status = -6;  // FW_ERR_NUMERIC
-        done = 1;
-    } else if (st->active == 0 || S[0] <= 0.0) {
-        status = 0;
-        done = 1;
-    } else {
-        const double thr = pd.tol_mode ? pd.gap_tol * st->g0 : pd.gap_tol;
-        if (S[0] <= thr) {
-            status = 0;
-            done = 1;
-        } else if (st->iter >= pd.max_iters) {
-            status = 1;  // FW_NOT_CONVERGED
-            done = 1;
-        }
-    }
-    st->status = status;
-    st->done = done;
-    if (done) return;
-    const double g = S[0];
-    const double qL = S[5] - S[3];                        // <D, L D>
-    const double q = qL + S[2] - 2.0 * pd.inv_eps * S[1];  // <D, H D>
-    if (!isfinite(q)) {
-        st->status = -6;
-        st->done = 1;
-        return;
-    }
-    double a = 1.0;
-    if (pd.step_rule == 0) {
-        if (q > 0.0) a = fmin(1.0, g / q);
-    } else {
-        // Armijo: largest 0.5^j with E(U) - E(U + a D) = a g - a^2 q / 2 >= 1e-6 a g
-        if (q > 0.0) {
-            const double amax = 2.0 * (1.0 - 1e-6) * g / q;
-            for (int j = 0; j < 1100 && a > amax; ++j) a *= 0.5;
-        }
-    }
-    st->q = q;
-    st->alpha = a;
-    st->alpha_f = float(a);
-    st->E = st->E - a * g + 0.5 * a * a * q;
-    st->iter += 1;
-    st->has_update = 1;
-}
-
-// Read this iteration's totals from the accumulators, clear them, and run
-// finish_iter (one thread).
-__device__ __forceinline__ void finish_from_acc(const ProbDesc& pd, ProbState* st) {
-    double S[kNumR];
-#pragma unroll
-    for (int q = 0; q < kNumR; ++q) S[q] = fx_total(pd.acc, q);
-    if (__ldcg(&pd.acc[kAccFlag])) S[0] = CUDART_NAN;
-#pragma unroll
-    for (int c = 0; c < kAccCopies * kNumR; ++c) {
-        pd.acc[c * kAccLine] = 0ull;
-        pd.acc[c * kAccLine + 1] = 0ull;
-    }
-    pd.acc[kAccFlag] = 0ull;
-    finish_iter(pd, st, S);
-}
-
 // ------------------------------------------------------------- row tiles
 // One row tile of pass A with its block reduction; the last tile of the
 // problem to finish runs the stop test.  `ndone` (nullable) counts problems
 // that stop in this pass.  Every thread of the block must call it.
 template <typename T, int KMAX, bool EXACT = false>
 __device__ __forceinline__ void tile_A(const ProbDesc& pd, ProbState* st, int tile, bool upd,
-                                       T alpha, T* stage, int nstages, uint64_t* bars,
-                                       uint32_t& phases) {
+                                       T alpha, const FuseCtl& fc, unsigned long long* accb,
+                                       T* stage, int nstages, uint64_t* bars, uint32_t& phases) {
     const int r0 = tile * pd.tile_rows;
     const int r1 = min(pd.n, r0 + pd.tile_rows);
     AccA<T> acc{T(0), T(0), T(0), T(0), T(0)};
-    if (!passA_staged<T, KMAX, EXACT>(pd, r0, r1, upd, alpha, acc, stage, nstages, bars, phases) &&
-        threadIdx.x == 0)
-        atomicExch(&st->err, 1);
+    const int rc =
+        passA_staged<T, KMAX, EXACT>(pd, r0, r1, upd, alpha, fc, acc, stage, nstages, bars, phases);
+    if (rc == kPassStopped) return;
+    if (rc == kPassTimeout && threadIdx.x == 0) atomicExch(&st->err, 1);
     const T v[kNumA] = {acc.g, acc.nD, acc.nW, acc.tLU, acc.act};
-    block_accumulate<T, kNumA>(v, pd.acc, 0, tile % kAccCopies);
+    block_accumulate<T, kNumA>(v, accb, 0, tile % kAccCopies);
 }
 
-// One row tile of pass B.  With LAST, the last tile of the problem to finish
-// runs finish_iter on the accumulated totals (persistent kernel); otherwise a
-// separate k_finish launch does that.  `ndone` (nullable) counts problems
-// that stop.
+// One row tile of pass B, accumulating into bank `accb`.  With LAST, the last
+// tile of the problem to finish takes the step decision on that bank
+// (persistent kernel); otherwise k_finish or the next pass A does.  `ndone`
+// (nullable) counts problems that stop.
 template <typename T, typename WT, int KMAX, bool RO, bool LAST, int LC = 0,
           bool EXACT = false>
 __device__ __forceinline__ void tile_B(const ProbDesc& pd, ProbState* st, int tile, T* sm_lane,
-                                       T* sm_row, uint32_t* ndone) {
+                                       T* sm_row, unsigned long long* accb, uint32_t* ndone) {
     const int r0 = tile * pd.tile_rows;
     const int r1 = min(pd.n, r0 + pd.tile_rows);
     T accq = T(0);
     passB_rows<T, WT, KMAX, RO, LC, EXACT>(pd, r0, r1, accq, sm_lane, sm_row);
     const T v[kNumB] = {accq};
-    block_accumulate<T, kNumB>(v, pd.acc, kNumA, tile % kAccCopies);
-    if (LAST && last_to_arrive(&st->cnt, pd.ntiles) && threadIdx.x == 0) {
-        st->cnt = 0;
-        finish_from_acc(pd, st);
-        if (ndone && st->done) atomicAdd(ndone, 1u);
+    block_accumulate<T, kNumB>(v, accb, kNumA, tile % kAccCopies);
+    if (LAST && last_to_arrive(&st->cnt, pd.ntiles) && threadIdx.x < 32) {
+        const int done = warp_finish(pd, st, accb);
+        if (threadIdx.x == 0) {
+            st->cnt = 0;
+            if (ndone && done) atomicAdd(ndone, 1u);
+        }
     }
 }
 

@@ -30,7 +30,9 @@ public:
     virtual size_t elem() const = 0;    // sizeof(T)
     virtual size_t welem() const = 0;   // sizeof(WT)
     virtual int kmax() const = 0;
-    virtual void passA(const ProbDesc& pd, ProbState* st, cudaStream_t s) = 0;
+    // fin: take the previous iteration's step decision inside this pass (the
+    // previous iteration then has no k_finish); 0: apply the stored step
+    virtual void passA(const ProbDesc& pd, ProbState* st, cudaStream_t s, int fin) = 0;
     virtual void passB(const ProbDesc& pd, ProbState* st, cudaStream_t s) = 0;
     // one thread: read the exact totals, stop test, step
     virtual void finish(const ProbDesc& pd, ProbState* st, cudaStream_t s) = 0;
@@ -78,6 +80,9 @@ struct HostGraph {
 struct ProbLayout {
     int64_t n = 0, nnz = 0, nnz_pad = 0, npad = 0;
     int32_t K = 0, tile_rows = 0, ntiles = 0, lanes = 1;
+    // keep the 4-bit class array (ProbDesc::cls4): set by the two-kernel
+    // single-problem path for K <= 16; the persistent kernels do not use it
+    bool cls4 = false;
 };
 
 // Host checks (options, row_ptr, labels) and the padded layout.
@@ -101,5 +106,7 @@ fw_status restart_problem(Ops* ops, const ProbDesc& pd, ProbState* st, bool from
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 int tile_rows_for(int64_t n);
 int default_lanes(double avg_padded_degree);
+// Lane count of the persistent kernels (batches, serving) unless the options fix it.
+void persistent_lanes(const fw_seg_opts& o, ProbLayout& lay);
 
 }  // namespace fw

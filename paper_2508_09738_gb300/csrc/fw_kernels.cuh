@@ -5,36 +5,96 @@
 namespace fw {
 
 // ---------------------------------------------------------------- hot loop
-// Pass A: one block per row tile; the last block runs the stop test.
+// Step pass A of one tile (k_passA, k_passA_k4).  With `fin` the block first
+// takes the previous iteration's step decision itself (no k_finish between
+// the passes; see ProbState); otherwise it applies the step k_finish stored.
+template <typename T, int KMAX, bool EXACT>
+__device__ __forceinline__ void passA_step(const ProbDesc& pd, ProbState* st, int fin, T* stage) {
+    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ double s_alpha;
+    __shared__ int s_stop;
+    const int done = ld_cg(&st->done);
+    const int c = ld_cg(&st->cur);
+    if (done) return;
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        if (fin) {   // the first copies go out at once (a step is always pending)
+            const int r0 = blockIdx.x * pd.tile_rows;
+            stage_issue<T, KMAX>(pd, r0, min(kBlock, pd.n - r0), true, stage, &bars[0]);
+        } else if (blockIdx.x == 0) {
+            st->cur_b = c;
+        }
+    }
+    if (fin && threadIdx.x < 32) {
+        // warp 0 takes the previous iteration's decision while the copies are
+        // in flight; block 0 commits it
+        double a;
+        const int stop = warp_decide(pd.acc + c * kAccBank, st, c, step_cfg(pd), blockIdx.x == 0, &a);
+        if (threadIdx.x == 0) {
+            s_stop = stop;
+            s_alpha = a;
+            if (blockIdx.x == 0) st->cur_b = c ^ 1;
+        }
+    }
+    const bool upd = fin ? true : ld_cg(&st->has_update) != 0;
+    const T alpha = fin ? T(0) : alpha_of<T>(st);
+    __syncthreads();
+    uint32_t phases = 0;
+    const int nst = (pd.tile_rows > kBlock && max_stages<T, KMAX>() == 2) ? 2 : 1;
+    const int bank = fin ? (c ^ 1) : c;
+    tile_A<T, KMAX, EXACT>(pd, st, blockIdx.x, upd, alpha, FuseCtl{fin != 0, &s_stop, &s_alpha},
+                           pd.acc + bank * kAccBank, stage, nst, bars, phases);
+}
+
+// Pass B entry: this iteration's bank (set by pass A); block 0 makes it the
+// pending bank and clears the other one, which the next pass A will fill.
+__device__ __forceinline__ unsigned long long* passB_bank(const ProbDesc& pd, ProbState* st,
+                                                          bool& done) {
+    const int b = ld_cg(&st->cur_b);
+    done = ld_cg(&st->done) != 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->cur = b;
+        unsigned long long* z = pd.acc + (b ^ 1) * kAccBank;
+#pragma unroll
+        for (int w = 0; w < kAccWords; ++w) z[w] = 0ull;
+    }
+    return pd.acc + b * kAccBank;
+}
+
+// Blocks of pass A that one SM holds by shared memory (one stage buffer; at
+// most 8, or 5 for an FP64 iterate, whose rows need more registers): the
+// register budget is set to match, so that the fused step decision does not
+// lower the occupancy.
+template <typename T, int KMAX>
+constexpr int passA_min_blocks() {
+    constexpr int cap = sizeof(T) == 8 ? 5 : 8;
+    constexpr int b = (227 * 1024) / (3 * kBlock * KMAX * int(sizeof(T)) + 1024);
+    return b < 1 ? 1 : (b > cap ? cap : b);
+}
+
+// Pass A: one block per row tile.
+//   MODE_STEP applies the pending step and evaluates (passA_step);
 //   MODE_FLUSH applies a pending step only; MODE_GRAD writes G' and the choice.
 template <typename T, int KMAX, int MODE>
-__global__ void __launch_bounds__(kBlock)
-    k_passA(ProbDesc pd, ProbState* st, T* Gout, uint8_t* chout) {
-    if (MODE != MODE_GRAD && ld_cg(&st->done)) return;
-    const bool upd = ld_cg(&st->has_update) != 0;
-    const T alpha = alpha_of<T>(st);
+__global__ void __launch_bounds__(kBlock, MODE == MODE_STEP ? passA_min_blocks<T, KMAX>() : 1)
+    k_passA(ProbDesc pd, ProbState* st, T* Gout, uint8_t* chout, int fin) {
     if constexpr (MODE == MODE_STEP) {
         extern __shared__ __align__(128) unsigned char smraw[];
-        __shared__ __align__(8) uint64_t bars[2];
-        if (threadIdx.x == 0) {
-            mbar_init(&bars[0], 1);
-            mbar_init(&bars[1], 1);
-        }
-        __syncthreads();
-        uint32_t phases = 0;
-        const int nst = (pd.tile_rows > kBlock && max_stages<T, KMAX>() == 2) ? 2 : 1;
-        tile_A<T, KMAX>(pd, st, blockIdx.x, upd, alpha, reinterpret_cast<T*>(smraw), nst, bars,
-                        phases);
-        return;
-    }
-    const int r0 = blockIdx.x * pd.tile_rows;
-    const int r1 = min(pd.n, r0 + pd.tile_rows);
-    AccA<T> acc{T(0), T(0), T(0), T(0), T(0)};
-    passA_rows<T, KMAX, MODE>(pd, r0, r1, upd, alpha, acc, Gout, chout);
-    if (MODE == MODE_FLUSH) {
-        if (last_to_arrive(&st->cntF, pd.ntiles) && threadIdx.x == 0) {
-            st->has_update = 0;
-            st->cntF = 0;
+        passA_step<T, KMAX, false>(pd, st, fin, reinterpret_cast<T*>(smraw));
+    } else {
+        if (MODE != MODE_GRAD && ld_cg(&st->done)) return;
+        const bool upd = ld_cg(&st->has_update) != 0;
+        const T alpha = alpha_of<T>(st);
+        const int r0 = blockIdx.x * pd.tile_rows;
+        const int r1 = min(pd.n, r0 + pd.tile_rows);
+        AccA<T> acc{T(0), T(0), T(0), T(0), T(0)};
+        passA_rows<T, KMAX, MODE>(pd, r0, r1, upd, alpha, acc, Gout, chout);
+        if (MODE == MODE_FLUSH) {
+            if (last_to_arrive(&st->cntF, pd.ntiles) && threadIdx.x == 0) {
+                st->has_update = 0;
+                st->cntF = 0;
+            }
         }
     }
 }
@@ -43,32 +103,22 @@ __global__ void __launch_bounds__(kBlock)
 // is fully known at compile time, which removes the per-class guards, and the
 // kernel is held to 32 registers so that 8 blocks per SM stay resident.
 template <typename T>
-__global__ void __launch_bounds__(kBlock, 8) k_passA_k4(ProbDesc pd, ProbState* st) {
+__global__ void __launch_bounds__(kBlock, 8) k_passA_k4(ProbDesc pd, ProbState* st, int fin) {
     extern __shared__ __align__(128) unsigned char smraw[];
-    __shared__ __align__(8) uint64_t bars[2];
-    if (ld_cg(&st->done)) return;
-    const bool upd = ld_cg(&st->has_update) != 0;
-    const T alpha = alpha_of<T>(st);
-    if (threadIdx.x == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
-    }
-    __syncthreads();
-    uint32_t phases = 0;
-    const int nst = (pd.tile_rows > kBlock && max_stages<T, 4>() == 2) ? 2 : 1;
-    tile_A<T, 4, true>(pd, st, blockIdx.x, upd, alpha, reinterpret_cast<T*>(smraw), nst, bars,
-                       phases);
+    passA_step<T, 4, true>(pd, st, fin, reinterpret_cast<T*>(smraw));
 }
 
 // Pass B: one block per row tile; each adds its tile total to the exact
 // accumulators (no block waits for another).
 template <typename T, typename WT, int KMAX>
 __global__ void __launch_bounds__(kBlock) k_passB(ProbDesc pd, ProbState* st) {
-    if (ld_cg(&st->done)) return;
+    bool done;
+    unsigned long long* accb = passB_bank(pd, st, done);
+    if (done) return;
     extern __shared__ __align__(128) unsigned char smraw[];
     T* sm_lane = reinterpret_cast<T*>(smraw);
     T* sm_row = sm_lane + kBlock * (KMAX | 1);
-    tile_B<T, WT, KMAX, true, false>(pd, st, blockIdx.x, sm_lane, sm_row, nullptr);
+    tile_B<T, WT, KMAX, true, false>(pd, st, blockIdx.x, sm_lane, sm_row, accb, nullptr);
 }
 
 // Pass B with LC lanes per row known at compile time (1 for low-degree graphs
@@ -76,19 +126,24 @@ __global__ void __launch_bounds__(kBlock) k_passB(ProbDesc pd, ProbState* st) {
 // Same sums, in the same order, as k_passB.
 template <typename T, typename WT, int KMAX, int LC, bool EXACT>
 __global__ void __launch_bounds__(kBlock) k_passB_lc(ProbDesc pd, ProbState* st) {
-    if (ld_cg(&st->done)) return;
+    bool done;
+    unsigned long long* accb = passB_bank(pd, st, done);
+    if (done) return;
     extern __shared__ __align__(128) unsigned char smraw[];
     T* sm_lane = reinterpret_cast<T*>(smraw);
     T* sm_row = sm_lane + kBlock * (KMAX | 1);
-    tile_B<T, WT, KMAX, true, false, LC, EXACT>(pd, st, blockIdx.x, sm_lane, sm_row, nullptr);
+    tile_B<T, WT, KMAX, true, false, LC, EXACT>(pd, st, blockIdx.x, sm_lane, sm_row, accb,
+                                                nullptr);
 }
 
 // One thread after pass B: read the iteration's totals (complete after the
-// kernel boundary), run the stop test and the step.  (Doing this in the last
-// block of pass B instead costs every block a fence and an arrival, which
-// measured slower than this launch.)
-static __global__ void k_finish(ProbDesc pd, ProbState* st) {
-    if (threadIdx.x == 0 && !ld_cg(&st->done)) finish_from_acc(pd, st);
+// kernel boundary, in bank cur), run the stop test and the step.  Inside a
+// captured graph only the last iteration ends with it; the others leave the
+// decision to the next pass A.  (Doing it in the last block of pass B instead
+// costs every block a fence and an arrival, which measured slower.)
+static __global__ void k_finish(ProbDesc pd, ProbState* st) {   // one warp
+    if (ld_cg(&st->done)) return;
+    warp_finish(pd, st, pd.acc + ld_cg(&st->cur) * kAccBank);
 }
 
 // One-Shot Frank-Wolfe (Alg. 4): labels of U_1 = GLMO(grad E(U_hat)) in one
@@ -231,14 +286,21 @@ __global__ void k_build(int64_t n, const int32_t* rp, const int32_t* col, const 
 // U_0 = U_hat (Sec. 5.1): e_c on fidelity rows, 1/K elsewhere; choice reset.
 template <typename T>
 __global__ void k_reinit(ProbDesc pd) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= pd.n) return;
-    const int c = pd.fid[r];
-    const T unif = T(1) / T(pd.K);
-    T* Ub = static_cast<T*>(pd.U);
-    for (int k = 0; k < pd.K; ++k)
-        Ub[(int64_t)k * pd.npad + r] = c >= 0 ? (k == c ? T(1) : T(0)) : unif;
-    pd.choice[r] = uint8_t(c >= 0 ? c : 0);
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;   // blockDim.x = kBlock
+    int cls = 0;
+    if (r < pd.n) {
+        const int c = pd.fid[r];
+        const T unif = T(1) / T(pd.K);
+        T* Ub = static_cast<T*>(pd.U);
+        for (int k = 0; k < pd.K; ++k)
+            Ub[(int64_t)k * pd.npad + r] = c >= 0 ? (k == c ? T(1) : T(0)) : unif;
+        cls = c >= 0 ? c : 0;
+        pd.choice[r] = uint8_t(cls);
+    }
+    if (pd.cls4) {
+        const int hi = __shfl_down_sync(0xffffffffu, cls, 1);
+        if ((r & 1) == 0 && r < pd.n) pd.cls4[r >> 1] = uint8_t(cls | (hi << 4));
+    }
 }
 
 }  // namespace fw

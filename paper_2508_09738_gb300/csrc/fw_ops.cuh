@@ -51,19 +51,22 @@ public:
         return cudaFuncSetAttribute(k_spmm<T, WT, KMAX>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem()));
     }
-    void passA(const ProbDesc& pd, ProbState* st, cudaStream_t s) override {
-        if (kExact4 && pd.K == 4)
-            k_passA_k4<T><<<pd.ntiles, kBlock, smemA(pd), s>>>(pd, st);
-        else
-            k_passA<T, KMAX, MODE_STEP><<<pd.ntiles, kBlock, smemA(pd), s>>>(pd, st, nullptr,
-                                                                             nullptr);
+    void passA(const ProbDesc& pd, ProbState* st, cudaStream_t s, int fin) override {
+        if constexpr (kExact4) {
+            if (pd.K == 4) {
+                k_passA_k4<T><<<pd.ntiles, kBlock, smemA(pd), s>>>(pd, st, fin);
+                return;
+            }
+        }
+        k_passA<T, KMAX, MODE_STEP><<<pd.ntiles, kBlock, smemA(pd), s>>>(pd, st, nullptr, nullptr,
+                                                                         fin);
     }
     void flush(const ProbDesc& pd, ProbState* st, cudaStream_t s) override {
-        k_passA<T, KMAX, MODE_FLUSH><<<pd.ntiles, kBlock, 0, s>>>(pd, st, nullptr, nullptr);
+        k_passA<T, KMAX, MODE_FLUSH><<<pd.ntiles, kBlock, 0, s>>>(pd, st, nullptr, nullptr, 0);
     }
     void grad(const ProbDesc& pd, ProbState* st, void* Gout, uint8_t* chout,
               cudaStream_t s) override {
-        k_passA<T, KMAX, MODE_GRAD><<<pd.ntiles, kBlock, 0, s>>>(pd, st, (T*)Gout, chout);
+        k_passA<T, KMAX, MODE_GRAD><<<pd.ntiles, kBlock, 0, s>>>(pd, st, (T*)Gout, chout, 0);
     }
     void passB(const ProbDesc& pd, ProbState* st, cudaStream_t s) override {
         const unsigned g = unsigned(pd.ntiles);

@@ -3,12 +3,14 @@
 // Device state of a handle (one GPU, resident for the handle's lifetime, one
 // allocation): padded CSR of the off-diagonal operator (int32 row_ptr / col,
 // WT weights), U, L U, L S in class-major layout (T[K][npad]), choice (uint8)
-// and fid (int8) per row, per-tile FP64 partial records, and one ProbState.
-// Pass A writes its per-tile records only; the last block of pass B reduces
-// the records of both passes, runs the stop test and computes the step.
+// and fid (int8) per row, 4-bit classes for K <= 16, two banks of exact
+// fixed-point totals, and one ProbState.  Both passes add their block totals
+// into the iteration's bank; the stop test and the step follow from the bank
+// (k_finish, or the next pass A inside a captured graph).
 // A solve launches a CUDA graph that holds `iters_per_launch` iterations
-// (pass A + pass B each) and reads back the 128-byte state after each launch;
-// nothing else crosses the host-device boundary during the iteration.
+// (pass A + pass B each, one k_finish at the end) and reads the state back
+// after each launch; nothing else crosses the host-device boundary during the
+// iterations.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -150,10 +152,15 @@ static fw_status direct_objective(fw_seg* h, double* E) {
 
 // One GFW iteration: pass A, pass B, finish (3 launches).
 static void iteration(fw_seg* h) {
-    h->ops->passA(h->pd, h->st, h->stream);
+    h->ops->passA(h->pd, h->st, h->stream, 0);
     h->ops->passB(h->pd, h->st, h->stream);
     h->ops->finish(h->pd, h->st, h->stream);
 }
+
+// Launches of one captured graph of m iterations: the step decision of each
+// iteration but the last is taken inside the next pass A, so only the last
+// iteration ends with k_finish.
+static int graph_launches(int m) { return 2 * m + 1; }
 
 static fw_status build_graph(fw_seg* h) {
     if (h->graph) {
@@ -163,8 +170,10 @@ static fw_status build_graph(fw_seg* h) {
     cudaGraph_t g = nullptr;
     FW_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
     for (int i = 0; i < h->opts.iters_per_launch; ++i) {
-        iteration(h);
+        h->ops->passA(h->pd, h->st, h->stream, i > 0 ? 1 : 0);
+        h->ops->passB(h->pd, h->st, h->stream);
     }
+    h->ops->finish(h->pd, h->st, h->stream);
     cudaError_t e = cudaStreamEndCapture(h->stream, &g);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
     e = cudaGraphInstantiate(&h->graph, g, 0);
@@ -234,6 +243,7 @@ size_t fw_seg_footprint(int64_t n, int64_t nnz, int32_t K, int32_t weight_dtype)
     lay.K = K;
     lay.tile_rows = tile_rows_for(n);
     lay.ntiles = int32_t((n + lay.tile_rows - 1) / lay.tile_rows);
+    lay.cls4 = K <= 16;
     size_t b = problem_bytes(lay, te, we, true);
     b += te * size_t(lay.npad) * size_t(K) + 5 * size_t(n) + 8 * size_t(n / kBlock + 1);
     // stream-ordered temporaries of create
@@ -254,6 +264,7 @@ fw_status fw_seg_create(fw_seg** out, int64_t n, const int32_t* row_ptr, const i
         const HostGraph g{n, row_ptr, col, w, K, labels};
         std::unique_ptr<fw_seg> h(new fw_seg());
         FW_TRY(plan_problem(g, o, h->lay));
+        h->lay.cls4 = K <= 16;   // pass B gathers 4-bit classes (KMAX <= 16 forms)
         FW_CUDA(cudaGetDevice(&h->device));
         h->opts = o;
         if (o.cuda_stream) {
@@ -306,7 +317,7 @@ fw_status fw_seg_solve(fw_seg* h, fw_seg_stats* stats) {
         const int remaining = h->opts.max_iters - h->h_state->iter;
         if (remaining >= m && h->graph) {
             FW_CUDA(cudaGraphLaunch(h->graph, h->stream));
-            h->launches += 3 * m;
+            h->launches += graph_launches(m);
         } else {
             // direct launches; the tail (< m iterations left) ends with one more
             // pass pair whose stop test, at the iteration cap, ends the solve
@@ -350,7 +361,7 @@ fw_status fw_seg_profile(fw_seg* h, int32_t iters, double* ms_a, double* ms_b, d
     if (rc == FW_OK) {
         for (int i = 0; i < iters; ++i) {
             cudaEventRecord(ev[3 * i], h->stream);
-            h->ops->passA(h->pd, h->st, h->stream);
+            h->ops->passA(h->pd, h->st, h->stream, 0);
             cudaEventRecord(ev[3 * i + 1], h->stream);
             h->ops->passB(h->pd, h->st, h->stream);
             cudaEventRecord(ev[3 * i + 2], h->stream);

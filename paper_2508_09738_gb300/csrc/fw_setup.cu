@@ -64,6 +64,7 @@ __global__ void __launch_bounds__(kBlock) k_state_init(ProbState* st, const doub
         ProbState z = {};
         z.status = 2;  // FW_PENDING
         z.E = S[0];
+        z.in[0].E = S[0];   // cur = 0: the first decision reads in[0]
         *st = z;
     }
 }
@@ -198,10 +199,27 @@ int tile_rows_for(int64_t n) {
 }
 
 
+// Lanes per CSR row in pass B from the mean padded row length.  Measured on a
+// GB300 over stochastic block models (K = 4, 10, 16; mean degree 6 to 45):
+// one lane wins up to about 16 padded entries, four lanes above (two lanes
+// were at best 2.6% ahead and up to 11% behind); wider only for much longer
+// rows.
 int default_lanes(double avg_padded_degree) {
-    int L = 1;
-    while (L < 32 && avg_padded_degree > 12.0 * L) L *= 2;
+    if (avg_padded_degree <= 16.0) return 1;
+    int L = 4;
+    while (L < 32 && avg_padded_degree > 24.0 * L) L *= 2;
     return L;
+}
+
+// The persistent kernel walks rows with a run-time lane count; there two
+// lanes per row from 12 padded entries measured best (four lanes lost 8% on
+// batches of k-NN graphs with 13 to 18 padded entries per row).
+void persistent_lanes(const fw_seg_opts& o, ProbLayout& lay) {
+    if (o.lanes_per_row || lay.n == 0) return;
+    const double avg = double(lay.nnz_pad) / double(lay.n);
+    int L = 1;
+    while (L < 32 && avg > 12.0 * L) L *= 2;
+    lay.lanes = L;
 }
 
 fw_status check_opts(const fw_seg_opts& o) {
@@ -315,7 +333,8 @@ size_t problem_bytes(const ProbLayout& lay, size_t te, size_t we, bool comb) {
     size_t b = a256(4 * (n + 1)) + a256(4 * size_t(lay.nnz_pad)) + a256(we * size_t(lay.nnz_pad));
     if (comb) b += a256(te * n);
     b += 3 * a256(te * np * K) + a256(n) + a256(n);
-    b += a256(8 * size_t(kAccWords));
+    if (lay.cls4) b += a256((n + 1) / 2);
+    b += a256(8 * size_t(kAccTotal));
     return b;
 }
 
@@ -338,8 +357,9 @@ void place_problem(char* base, const ProbLayout& lay, size_t te, size_t we, cons
     pd.LU = take(te * np * K);
     pd.LS = take(te * np * K);
     pd.choice = reinterpret_cast<uint8_t*>(take(n));
+    pd.cls4 = lay.cls4 ? reinterpret_cast<uint8_t*>(take((n + 1) / 2)) : nullptr;
     pd.fid = reinterpret_cast<const int8_t*>(take(n));
-    pd.acc = reinterpret_cast<unsigned long long*>(take(8 * size_t(kAccWords)));
+    pd.acc = reinterpret_cast<unsigned long long*>(take(8 * size_t(kAccTotal)));
     pd.n = int32_t(lay.n);
     pd.npad = int32_t(lay.npad);
     pd.K = lay.K;
@@ -401,7 +421,7 @@ fw_status restart_problem(Ops* ops, const ProbDesc& pd, ProbState* st, bool from
     double* opart = nullptr;
     FW_TRYS(t.get(&opart, 8 * size_t(nb)));
     if (!from_current) ops->reinit(pd, s);
-    FW_CUDA(cudaMemsetAsync(pd.acc, 0, 8 * size_t(kAccWords), s));
+    FW_CUDA(cudaMemsetAsync(pd.acc, 0, 8 * size_t(kAccTotal), s));
     ops->spmm(pd, pd.U, pd.LU, s);
     ops->objective(pd, pd.LU, opart, s);
     k_state_init<<<1, kBlock, 0, s>>>(st, opart, nb);

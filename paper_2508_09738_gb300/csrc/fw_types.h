@@ -19,6 +19,12 @@ constexpr int kAccCopies = 1;
 constexpr int kAccLine = 2;                               // 8-byte words per slot
 constexpr int kAccFlag = kAccCopies * kNumR * kAccLine;   // index of the flag word
 constexpr int kAccWords = kAccFlag + kAccLine;
+// Two such banks, 128 bytes apart: iteration t accumulates into one while the
+// totals of iteration t-1 are still read from the other (the step decision of
+// t-1 is taken inside pass A of t; see ProbState::cur).
+constexpr int kAccBank = 16;
+constexpr int kAccTotal = 2 * kAccBank;
+static_assert(kAccWords <= kAccBank, "accumulator bank overflows its 128 bytes");
 
 // One problem on the device.  Every array is the problem's own (row-local
 // indexing, column indices local to the problem); in a batch they are slices
@@ -34,9 +40,11 @@ struct ProbDesc {
     void* LU;            // T[K][npad], L U by recurrence
     void* LS;            // T[K][npad], L S of the last step
     uint8_t* choice;     // [n] class chosen by the last evaluation | kActiveBit
+    uint8_t* cls4;       // [(n+1)/2] the same classes as 4-bit pairs (row 2m low nibble,
+                         // 2m+1 high) for K <= 16, gathered by pass B; NULL for K > 16
     const int8_t* fid;   // [n] fidelity class or -1
-    unsigned long long* acc;  // [kAccWords] Q64.64 totals of this iteration (see kAccCopies)
-                              // and a non-finite flag; exact and order-free
+    unsigned long long* acc;  // [kAccTotal]: two banks of kAccWords Q64.64 totals (see
+                              // kAccCopies) and a non-finite flag; exact and order-free
     int32_t n;           // rows
     int32_t npad;        // class stride of the SoA block (multiple of 32)
     int32_t K;           // classes
@@ -57,8 +65,35 @@ struct ProbDesc {
     float omf;           // omega0 as float
 };
 
-// Mutable per-problem state, in device memory.  Written only by the last
-// block to finish a pass of the problem, read by all blocks of the next pass.
+// The inputs of a step decision besides the iteration's totals: the running
+// objective, g_0 for the relative stop rule, and the updates applied so far.
+struct StepIn {
+    double E, g0;
+    int32_t iter, g0_set;
+};
+
+// Mutable per-problem state, in device memory.  The first block (iterate
+// fields) or the single finishing thread writes it; the next pass reads it.
+//
+// Step decisions.  Iteration t's totals complete when its pass B ends; the
+// stop test and the step length that follow from them are needed by pass A of
+// t+1.  Either a one-thread k_finish takes the decision between the passes,
+// or (inside a captured graph) every block of pass A of t+1 takes the same
+// decision from the same totals and inputs, and only its first block writes
+// the result here.  So that no block reads a field another block of the same
+// pass writes, the inputs are kept twice (in[cur] is read, in[cur ^ 1]
+// written) and the totals alternate between the two accumulator banks:
+//   pass A (decision fused): reads bank cur and in[cur], accumulates into
+//                            bank cur ^ 1, block 0 writes in[cur ^ 1] and
+//                            cur_b = cur ^ 1;
+//   pass A (plain):          accumulates into bank cur, block 0 writes
+//                            cur_b = cur;
+//   pass B:                  accumulates into bank cur_b; block 0 sets
+//                            cur = cur_b and clears bank cur_b ^ 1;
+//   k_finish:                reads and clears bank cur, reads in[cur], writes
+//                            in[cur ^ 1], cur ^= 1.
+// The persistent batch kernel always accumulates into bank 0 and decides in
+// its last block; it uses in[] / cur the same way.
 struct ProbState {
     double g, g0, nD, nW, tLU, pLS, q, alpha, E;
     float alpha_f;       // alpha rounded to float, for the FP32 update
@@ -71,7 +106,9 @@ struct ProbState {
     int32_t g0_set;
     uint32_t cnt;        // pass-B tiles arrived (the last one finishes the iteration)
     uint32_t cntF;       // flush tiles arrived
-    uint32_t pad0_, pad1_;
+    int32_t cur;         // parity: step inputs in[cur]; bank of the pending totals
+    int32_t cur_b;       // accumulator bank of the running iteration's pass B
+    StepIn in[2];
 };
 
 }  // namespace fw

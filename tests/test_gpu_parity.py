@@ -374,6 +374,46 @@ def test_graph_launch_equals_stepwise(blobs2k):
     assert np.array_equal(U1, U2)
 
 
+def _stepwise(g, **opts):
+    with B.Segmenter(g, **opts) as s:
+        st = None
+        for _ in range(opts["max_iters"] + 2):
+            st = s.step(1)
+            if st.status != B.FW_PENDING:
+                break
+        return s.U(), st
+
+
+@pytest.mark.parametrize("case", ["blobs_f64_rel", "image_k4_f32", "sbm_k10_f32_armijo"])
+@pytest.mark.parametrize("ipl", [7, 16])
+def test_fused_decisions_equal_stepwise(case, ipl):
+    """Inside a captured graph the step decision of each iteration but the
+    last is taken by the next pass A (two accumulator banks, double-buffered
+    inputs); direct launches take it in k_finish.  Same bits either way,
+    including a stop that lands in the middle of a graph."""
+    if case == "blobs_f64_rel":
+        g = W.blobs_knn(n=3001, K=6, seed=21, label_frac=0.03)
+        opts = dict(weight_dtype="f64", tol_mode="rel", gap_tol=0.075, max_iters=400)
+    elif case == "image_k4_f32":
+        g = W.voronoi_image(side=96, K=4, label_frac=0.01, seed=5)   # exact-4 pass A
+        opts = dict(weight_dtype="f32", tol_mode="rel", gap_tol=0.49, max_iters=400,
+                    omega0=1e5)
+    else:
+        g = W.sbm(n=20_000, K=10, deg_in=20.0, deg_out=2.0, label_frac=0.01, seed=4)
+        opts = dict(weight_dtype="f32", step_rule="armijo", max_iters=90, lanes_per_row=4)
+    U2, st2 = _stepwise(g, **opts)
+    with B.Segmenter(g, iters_per_launch=ipl, **opts) as s:
+        st1 = s.solve()
+        U1 = s.U()
+        assert s.stats().iters == st1.iters
+    assert st1.iters == st2.iters
+    assert st1.status == st2.status
+    assert st1.gap == st2.gap and st1.objective == st2.objective and st1.alpha == st2.alpha
+    assert np.array_equal(U1, U2)
+    if case != "sbm_k10_f32_armijo":
+        assert st1.status == B.FW_OK
+
+
 def test_set_U_roundtrip_and_lockstep(blobs2k):
     rng = np.random.default_rng(3)
     U = rng.dirichlet(np.ones(blobs2k.K), size=blobs2k.n)
