@@ -617,7 +617,6 @@ fw_status fw_batch_create(fw_batch** out, int32_t P, const fw_graph* graphs,
             const fw_graph& g = graphs[p];
             const HostGraph hg{g.n, g.row_ptr_host, g.col_host, g.w_host, g.K, g.labels_host};
             FW_TRY(plan_problem(hg, o, lays[size_t(p)]));
-            persistent_lanes(o, lays[size_t(p)]);
             Kmax = std::max(Kmax, g.K);
             b->max_iters = std::max(b->max_iters, o.max_iters);
             const size_t te = b->bo.weight_dtype == FW_WEIGHTS_F64 ? 8 : 4;
@@ -926,7 +925,6 @@ fw_status fw_srv_submit(fw_srv* s, const fw_graph* g, const fw_seg_opts* opts, u
         std::unique_ptr<Request> rq(new Request());
         const HostGraph hg{g->n, g->row_ptr_host, g->col_host, g->w_host, g->K, g->labels_host};
         FW_TRY(plan_problem(hg, o, rq->lay));
-        persistent_lanes(o, rq->lay);
         rq->bytes = s->eng.bytes_for(rq->lay, o);
         if (rq->bytes + 256 > s->eng.ra.cap()) {
             set_error("request can never fit the server's device pool");

@@ -106,7 +106,5 @@ fw_status restart_problem(Ops* ops, const ProbDesc& pd, ProbState* st, bool from
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 int tile_rows_for(int64_t n);
 int default_lanes(double avg_padded_degree);
-// Lane count of the persistent kernels (batches, serving) unless the options fix it.
-void persistent_lanes(const fw_seg_opts& o, ProbLayout& lay);
 
 }  // namespace fw

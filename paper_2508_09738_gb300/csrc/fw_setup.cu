@@ -200,26 +200,17 @@ int tile_rows_for(int64_t n) {
 
 
 // Lanes per CSR row in pass B from the mean padded row length.  Measured on a
-// GB300 over stochastic block models (K = 4, 10, 16; mean degree 6 to 45):
-// one lane wins up to about 16 padded entries, four lanes above (two lanes
-// were at best 2.6% ahead and up to 11% behind); wider only for much longer
-// rows.
+// GB300 (whole solves of stochastic block models with K = 4, 10, 16 and mean
+// degree 12 to 30): one lane wins up to about 20 padded entries (by up to 15%
+// at 13); from 20 to 32 entries two lanes stay within 2.2% of the best, while
+// one lane falls up to 20% behind at 32; four lanes pay off only for longer
+// rows.  The persistent kernels use the same count (so batched and single
+// solves agree bit for bit); on batches of k-NN graphs with 13 to 18 padded
+// entries one and two lanes measured the same there, four lanes 8% slower.
 int default_lanes(double avg_padded_degree) {
-    if (avg_padded_degree <= 16.0) return 1;
-    int L = 4;
-    while (L < 32 && avg_padded_degree > 24.0 * L) L *= 2;
-    return L;
-}
-
-// The persistent kernel walks rows with a run-time lane count; there two
-// lanes per row from 12 padded entries measured best (four lanes lost 8% on
-// batches of k-NN graphs with 13 to 18 padded entries per row).
-void persistent_lanes(const fw_seg_opts& o, ProbLayout& lay) {
-    if (o.lanes_per_row || lay.n == 0) return;
-    const double avg = double(lay.nnz_pad) / double(lay.n);
     int L = 1;
-    while (L < 32 && avg > 12.0 * L) L *= 2;
-    lay.lanes = L;
+    while (L < 32 && avg_padded_degree > 20.0 * L) L *= 2;
+    return L;
 }
 
 fw_status check_opts(const fw_seg_opts& o) {
