@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(kBlock) k_passB(ProbDesc pd, ProbState* st) {
 // such as images, 2 or 4 for denser ones); EXACT for exactly KMAX classes.
 // Same sums, in the same order, as k_passB.
 template <typename T, typename WT, int KMAX, int LC, bool EXACT>
-__global__ void __launch_bounds__(kBlock) k_passB_lc(ProbDesc pd, ProbState* st) {
+__device__ __forceinline__ void passB_lc_body(const ProbDesc& pd, ProbState* st) {
     bool done;
     unsigned long long* accb = passB_bank(pd, st, done);
     if (done) return;
@@ -134,6 +134,20 @@ __global__ void __launch_bounds__(kBlock) k_passB_lc(ProbDesc pd, ProbState* st)
     T* sm_row = sm_lane + kBlock * (KMAX | 1);
     tile_B<T, WT, KMAX, true, false, LC, EXACT>(pd, st, blockIdx.x, sm_lane, sm_row, accb,
                                                 nullptr);
+}
+
+template <typename T, typename WT, int KMAX, int LC, bool EXACT>
+__global__ void __launch_bounds__(kBlock) k_passB_lc(ProbDesc pd, ProbState* st) {
+    passB_lc_body<T, WT, KMAX, LC, EXACT>(pd, st);
+}
+
+// The 2- and 4-lane forms for 5 to 12 classes of FP32 need 44-48 registers,
+// i.e. 5 blocks per SM, and a problem with more tiles than 5 x 152 then runs
+// a second wave (sbm200k: 782 tiles).  Held to 40 registers (6 blocks per SM,
+// a few spilled words) they measured 7% faster there.
+template <typename T, typename WT, int KMAX, int LC, bool EXACT>
+__global__ void __launch_bounds__(kBlock, 6) k_passB_lc6(ProbDesc pd, ProbState* st) {
+    passB_lc_body<T, WT, KMAX, LC, EXACT>(pd, st);
 }
 
 // One thread after pass B: read the iteration's totals (complete after the

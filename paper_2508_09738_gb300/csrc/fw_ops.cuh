@@ -10,6 +10,8 @@ class OpsImpl final : public Ops {
 public:
     // four classes, FP32 iterate: the compile-time class-count pass A
     static constexpr bool kExact4 = KMAX == 4 && sizeof(T) == 4;
+    // 2 / 4 lanes per row, 5..12 classes, FP32 iterate: the 40-register pass B
+    static constexpr bool kBound6 = sizeof(T) == 4 && KMAX >= 8 && KMAX <= 12;
     size_t elem() const override { return sizeof(T); }
     size_t welem() const override { return sizeof(WT); }
     int kmax() const override { return KMAX; }
@@ -39,7 +41,8 @@ public:
                                  int(smem()));
         if (e != cudaSuccess) return e;
         for (auto f : {k_passB_lc<T, WT, KMAX, 1, false>, k_passB_lc<T, WT, KMAX, 2, false>,
-                       k_passB_lc<T, WT, KMAX, 4, false>}) {
+                       k_passB_lc<T, WT, KMAX, 4, false>, k_passB_lc6<T, WT, KMAX, 2, false>,
+                       k_passB_lc6<T, WT, KMAX, 4, false>}) {
             e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem()));
             if (e != cudaSuccess) return e;
         }
@@ -74,6 +77,10 @@ public:
             k_passB_lc<T, WT, 4, 1, true><<<g, kBlock, smem(), s>>>(pd, st);
         else if (pd.lanes == 1)
             k_passB_lc<T, WT, KMAX, 1, false><<<g, kBlock, smem(), s>>>(pd, st);
+        else if (pd.lanes == 2 && kBound6)
+            k_passB_lc6<T, WT, KMAX, 2, false><<<g, kBlock, smem(), s>>>(pd, st);
+        else if (pd.lanes == 4 && kBound6)
+            k_passB_lc6<T, WT, KMAX, 4, false><<<g, kBlock, smem(), s>>>(pd, st);
         else if (pd.lanes == 2)
             k_passB_lc<T, WT, KMAX, 2, false><<<g, kBlock, smem(), s>>>(pd, st);
         else if (pd.lanes == 4)
