@@ -183,6 +183,7 @@ BatchKern* make_batch_kern_t(int kmax) {
     switch (kmax) {
         case 4: return new BatchKernImpl<T, WT, 4>();
         case 8: return new BatchKernImpl<T, WT, 8>();
+        case 10: return new BatchKernImpl<T, WT, 10>();
         case 12: return new BatchKernImpl<T, WT, 12>();
         case 16: return new BatchKernImpl<T, WT, 16>();
         case 32: return new BatchKernImpl<T, WT, 32>();

@@ -59,7 +59,7 @@ __global__ void k_validate(int64_t n, const int32_t* rp, const int32_t* col, con
 __global__ void k_state_init(ProbState* st, const double* part, int nb);
 __global__ void k_fid(int64_t n, const int32_t* labels, int8_t* fid);
 
-// Factories, one per translation unit.  kmax in {4, 8, 12, 16, 32}.
+// Factories, one per translation unit.  kmax in {4, 8, 10, 12, 16, 32}.
 Ops* make_ops_f32(int kmax);
 Ops* make_ops_bf16(int kmax);
 Ops* make_ops_f64(int kmax);

@@ -99,13 +99,14 @@ __global__ void __launch_bounds__(kBlock, MODE == MODE_STEP ? passA_min_blocks<T
     }
 }
 
-// Pass A (step) for exactly four classes with an FP32 iterate: the class loop
-// is fully known at compile time, which removes the per-class guards, and the
-// kernel is held to 32 registers so that 8 blocks per SM stay resident.
-template <typename T>
-__global__ void __launch_bounds__(kBlock, 8) k_passA_k4(ProbDesc pd, ProbState* st, int fin) {
+// Pass A (step) for exactly KMAX classes with an FP32 iterate: the class loop
+// is fully known at compile time, which removes the per-class guards.  Used
+// for four classes, where it is held to 32 registers (8 blocks per SM).
+template <typename T, int KMAX>
+__global__ void __launch_bounds__(kBlock, passA_min_blocks<T, KMAX>())
+    k_passA_exact(ProbDesc pd, ProbState* st, int fin) {
     extern __shared__ __align__(128) unsigned char smraw[];
-    passA_step<T, 4, true>(pd, st, fin, reinterpret_cast<T*>(smraw));
+    passA_step<T, KMAX, true>(pd, st, fin, reinterpret_cast<T*>(smraw));
 }
 
 // Pass B: one block per row tile; each adds its tile total to the exact

@@ -8,8 +8,11 @@ namespace fw {
 template <typename T, typename WT, int KMAX>
 class OpsImpl final : public Ops {
 public:
-    // four classes, FP32 iterate: the compile-time class-count pass A
-    static constexpr bool kExact4 = KMAX == 4 && sizeof(T) == 4;
+    // exactly KMAX classes, FP32 iterate: the compile-time class-count forms
+    // (pass A only for four classes: with more, the fully unrolled row keeps
+    // its classes in registers and spills at the occupancy it needs)
+    static constexpr bool kExactA = sizeof(T) == 4 && KMAX == 4;
+    static constexpr bool kExactB = sizeof(T) == 4 && KMAX <= 12;
     // 2 / 4 lanes per row, 5..12 classes, FP32 iterate: the 40-register pass B
     static constexpr bool kBound6 = sizeof(T) == 4 && KMAX >= 8 && KMAX <= 12;
     size_t elem() const override { return sizeof(T); }
@@ -29,9 +32,9 @@ public:
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              int(smemA()));
         if (e != cudaSuccess) return e;
-        if constexpr (kExact4) {
-            e = cudaFuncSetAttribute(k_passA_k4<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     int(smemA()));
+        if constexpr (kExactA) {
+            e = cudaFuncSetAttribute(k_passA_exact<T, KMAX>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, int(smemA()));
             if (e != cudaSuccess) return e;
         }
         e = cudaFuncSetAttribute(k_passB<T, WT, KMAX>,
@@ -46,18 +49,22 @@ public:
             e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem()));
             if (e != cudaSuccess) return e;
         }
-        if constexpr (kExact4) {
-            e = cudaFuncSetAttribute(k_passB_lc<T, WT, 4, 1, true>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem()));
-            if (e != cudaSuccess) return e;
+        if constexpr (kExactB) {
+            for (auto f : {k_passB_lc<T, WT, KMAX, 1, true>, k_passB_lc<T, WT, KMAX, 2, true>,
+                           k_passB_lc<T, WT, KMAX, 4, true>, k_passB_lc6<T, WT, KMAX, 2, true>,
+                           k_passB_lc6<T, WT, KMAX, 4, true>}) {
+                e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(smem()));
+                if (e != cudaSuccess) return e;
+            }
         }
         return cudaFuncSetAttribute(k_spmm<T, WT, KMAX>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem()));
     }
     void passA(const ProbDesc& pd, ProbState* st, cudaStream_t s, int fin) override {
-        if constexpr (kExact4) {
-            if (pd.K == 4) {
-                k_passA_k4<T><<<pd.ntiles, kBlock, smemA(pd), s>>>(pd, st, fin);
+        if constexpr (kExactA) {
+            if (pd.K == KMAX) {
+                k_passA_exact<T, KMAX><<<pd.ntiles, kBlock, smemA(pd), s>>>(pd, st, fin);
                 return;
             }
         }
@@ -71,22 +78,32 @@ public:
               cudaStream_t s) override {
         k_passA<T, KMAX, MODE_GRAD><<<pd.ntiles, kBlock, 0, s>>>(pd, st, (T*)Gout, chout, 0);
     }
-    void passB(const ProbDesc& pd, ProbState* st, cudaStream_t s) override {
+    template <bool EXACT>
+    void passB_lanes(const ProbDesc& pd, ProbState* st, cudaStream_t s) {
         const unsigned g = unsigned(pd.ntiles);
-        if (pd.lanes == 1 && kExact4 && pd.K == 4)
-            k_passB_lc<T, WT, 4, 1, true><<<g, kBlock, smem(), s>>>(pd, st);
-        else if (pd.lanes == 1)
-            k_passB_lc<T, WT, KMAX, 1, false><<<g, kBlock, smem(), s>>>(pd, st);
+        if (pd.lanes == 1)
+            k_passB_lc<T, WT, KMAX, 1, EXACT><<<g, kBlock, smem(), s>>>(pd, st);
         else if (pd.lanes == 2 && kBound6)
-            k_passB_lc6<T, WT, KMAX, 2, false><<<g, kBlock, smem(), s>>>(pd, st);
+            k_passB_lc6<T, WT, KMAX, 2, EXACT><<<g, kBlock, smem(), s>>>(pd, st);
         else if (pd.lanes == 4 && kBound6)
-            k_passB_lc6<T, WT, KMAX, 4, false><<<g, kBlock, smem(), s>>>(pd, st);
+            k_passB_lc6<T, WT, KMAX, 4, EXACT><<<g, kBlock, smem(), s>>>(pd, st);
         else if (pd.lanes == 2)
-            k_passB_lc<T, WT, KMAX, 2, false><<<g, kBlock, smem(), s>>>(pd, st);
-        else if (pd.lanes == 4)
-            k_passB_lc<T, WT, KMAX, 4, false><<<g, kBlock, smem(), s>>>(pd, st);
+            k_passB_lc<T, WT, KMAX, 2, EXACT><<<g, kBlock, smem(), s>>>(pd, st);
         else
-            k_passB<T, WT, KMAX><<<g, kBlock, smem(), s>>>(pd, st);
+            k_passB_lc<T, WT, KMAX, 4, EXACT><<<g, kBlock, smem(), s>>>(pd, st);
+    }
+    void passB(const ProbDesc& pd, ProbState* st, cudaStream_t s) override {
+        if (pd.lanes != 1 && pd.lanes != 2 && pd.lanes != 4) {
+            k_passB<T, WT, KMAX><<<unsigned(pd.ntiles), kBlock, smem(), s>>>(pd, st);
+            return;
+        }
+        if constexpr (kExactB) {
+            if (pd.K == KMAX) {
+                passB_lanes<true>(pd, st, s);
+                return;
+            }
+        }
+        passB_lanes<false>(pd, st, s);
     }
     void finish(const ProbDesc& pd, ProbState* st, cudaStream_t s) override {
         k_finish<<<1, 32, 0, s>>>(pd, st);
@@ -123,6 +140,7 @@ Ops* make_ops_t(int kmax) {
     switch (kmax) {
         case 4: return new OpsImpl<T, WT, 4>();
         case 8: return new OpsImpl<T, WT, 8>();
+        case 10: return new OpsImpl<T, WT, 10>();
         case 12: return new OpsImpl<T, WT, 12>();
         case 16: return new OpsImpl<T, WT, 16>();
         case 32: return new OpsImpl<T, WT, 32>();

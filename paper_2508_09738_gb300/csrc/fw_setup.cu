@@ -180,7 +180,9 @@ static fw_status invalid(const std::string& m) {
 }
 
 // ------------------------------------------------------------- choices
-int kmax_for(int K) { return K <= 4 ? 4 : K <= 8 ? 8 : K <= 12 ? 12 : K <= 16 ? 16 : 32; }
+int kmax_for(int K) {
+    return K <= 4 ? 4 : K <= 8 ? 8 : K <= 10 ? 10 : K <= 12 ? 12 : K <= 16 ? 16 : 32;
+}
 
 Ops* make_ops(int weight_dtype, int K) {
     const int km = kmax_for(K);
