@@ -5,7 +5,7 @@
 namespace fw {
 
 // ---------------------------------------------------------------- hot loop
-// Step pass A of one tile (k_passA, k_passA_k4).  With `fin` the block first
+// Step pass A of one tile (k_passA, k_passA_exact).  With `fin` the block first
 // takes the previous iteration's step decision itself (no k_finish between
 // the passes; see ProbState); otherwise it applies the step k_finish stored.
 template <typename T, int KMAX, bool EXACT>
