@@ -1053,7 +1053,7 @@ __device__ __forceinline__ void passB_rows(const ProbDesc& pd, int r_begin, int 
 }
 
 // OUT = L X for rows [r_begin, r_end) (SoA in and out; OUT may not alias X).
-template <typename T, typename WT, int KMAX>
+template <typename T, typename WT, int KMAX, int SRC = kSrcDense>
 __device__ __forceinline__ void spmm_rows(const ProbDesc& pd, const T* __restrict__ X,
                                           T* __restrict__ OUT, int r_begin, int r_end, T* sm_lane,
                                           T* sm_row) {
@@ -1062,7 +1062,10 @@ __device__ __forceinline__ void spmm_rows(const ProbDesc& pd, const T* __restric
     const int64_t np = pd.npad;
     const T* __restrict__ diag = static_cast<const T*>(pd.diag);
     for (int base = r_begin; base < r_end; base += kBlock) {
-        csr_bins<T, WT, KMAX, kSrcDense, true>(pd, X, base, r_end, sm_lane, sm_row);
+        // X == U_hat (the stored U_0): its off-diagonal product comes from the
+        // fidelity bytes, bitwise the dense product (see csr_bins)
+        csr_bins<T, WT, KMAX, SRC, true>(pd, SRC == kSrcDense ? X : nullptr, base, r_end, sm_lane,
+                                         sm_row);
         const int r = base + threadIdx.x;
         if (r < r_end) {
             const T dg = pd.comb ? diag[r] : T(1);

@@ -40,6 +40,8 @@ public:
     virtual void grad(const ProbDesc& pd, ProbState* st, void* Gout, uint8_t* chout,
                       cudaStream_t s) = 0;
     virtual void spmm(const ProbDesc& pd, const void* X, void* out, cudaStream_t s) = 0;
+    // out = L U_hat, valid while U holds U_hat (right after reinit)
+    virtual void spmm_hat(const ProbDesc& pd, void* out, cudaStream_t s) = 0;
     // classic FW gap partials per row block (fresh LUf)
     virtual void lmo_gap(const ProbDesc& pd, const void* LUf, double* part, cudaStream_t s) = 0;
     // One-Shot Frank-Wolfe labels (Alg. 4) in one CSR pass

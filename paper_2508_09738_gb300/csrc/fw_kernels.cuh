@@ -185,6 +185,21 @@ __global__ void __launch_bounds__(kBlock) k_spmm(ProbDesc pd, const T* X, T* OUT
     spmm_rows<T, WT, KMAX>(pd, X, OUT, r0, r1, sm_lane, sm_row);
 }
 
+// L U_0 for U_0 = U_hat (the state reinit writes): the off-diagonal product
+// from the fidelity bytes (an unlabelled neighbour adds w/K to every class, a
+// labelled one w to its class), bitwise the dense SpMM of U_hat and without
+// its K gathers per entry.
+template <typename T, typename WT, int KMAX>
+__global__ void __launch_bounds__(kBlock) k_spmm_hat(ProbDesc pd, T* OUT) {
+    extern __shared__ __align__(128) unsigned char smraw[];
+    T* sm_lane = reinterpret_cast<T*>(smraw);
+    T* sm_row = sm_lane + kBlock * (KMAX | 1);
+    const int r0 = blockIdx.x * pd.tile_rows;
+    const int r1 = min(pd.n, r0 + pd.tile_rows);
+    spmm_rows<T, WT, KMAX, kSrcUhat>(pd, static_cast<const T*>(pd.U), OUT, r0, r1, sm_lane,
+                                     sm_row);
+}
+
 // ------------------------------------------------------------ read-outs
 // labels[i] = argmax_k u_ik, lowest index on ties.
 template <typename T>

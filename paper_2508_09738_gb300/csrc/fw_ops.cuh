@@ -58,6 +58,9 @@ public:
                 if (e != cudaSuccess) return e;
             }
         }
+        e = cudaFuncSetAttribute(k_spmm_hat<T, WT, KMAX>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem()));
+        if (e != cudaSuccess) return e;
         return cudaFuncSetAttribute(k_spmm<T, WT, KMAX>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem()));
     }
@@ -110,6 +113,9 @@ public:
     }
     void oneshot(const ProbDesc& pd, int32_t* labels, cudaStream_t s) override {
         k_osfw<T, WT, KMAX><<<rows_grid(pd), kBlock, smem(), s>>>(pd, labels);
+    }
+    void spmm_hat(const ProbDesc& pd, void* out, cudaStream_t s) override {
+        k_spmm_hat<T, WT, KMAX><<<pd.ntiles, kBlock, smem(), s>>>(pd, (T*)out);
     }
     void spmm(const ProbDesc& pd, const void* X, void* out, cudaStream_t s) override {
         k_spmm<T, WT, KMAX><<<pd.ntiles, kBlock, smem(), s>>>(pd, (const T*)X, (T*)out);

@@ -53,6 +53,8 @@ struct fw_seg {
     ProbDesc pd{};
     ProbState* st = nullptr;        // device
     ProbState* h_state = nullptr;   // pinned mirror
+    ProbState* h_ring = nullptr;    // pinned [2]: state copies of queued graph launches
+    cudaEvent_t ring_ev[2] = {nullptr, nullptr};
     char* mem = nullptr;            // the problem's arrays
     void* d_tmp = nullptr;          // T[K][npad]: fresh L U, gradient
     uint8_t* d_ch = nullptr;        // choice scratch of fw_seg_get_grad
@@ -83,6 +85,9 @@ struct fw_seg {
         if (graph) cudaGraphExecDestroy(graph);
         for (void* p : dev_allocs) cudaFree(p);
         if (h_state) cudaFreeHost(h_state);
+        if (h_ring) cudaFreeHost(h_ring);
+        for (cudaEvent_t e : ring_ev)
+            if (e) cudaEventDestroy(e);
         if (ev0) cudaEventDestroy(ev0);
         if (ev1) cudaEventDestroy(ev1);
         if (own_stream && stream) cudaStreamDestroy(stream);
@@ -277,6 +282,9 @@ fw_status fw_seg_create(fw_seg** out, int64_t n, const int32_t* row_ptr, const i
         if (!h->ops) return invalid("no kernels for this weight dtype / K");
         FW_CUDA(h->ops->configure());
         FW_CUDA(cudaMallocHost(&h->h_state, sizeof(ProbState)));
+        FW_CUDA(cudaMallocHost(&h->h_ring, 2 * sizeof(ProbState)));
+        for (cudaEvent_t& e : h->ring_ev)
+            FW_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         FW_CUDA(cudaEventCreate(&h->ev0));
         FW_CUDA(cudaEventCreate(&h->ev1));
         const size_t te = h->ops->elem(), we = h->ops->welem();
@@ -311,19 +319,50 @@ fw_status fw_seg_solve(fw_seg* h, fw_seg_stats* stats) {
     FW_CUDA(cudaEventRecord(h->ev0, h->stream));
     FW_TRY(read_state(h));
     const int m = h->opts.iters_per_launch;
+    const int R = h->opts.refresh_every;
+    if (h->graph && R <= 0) {
+        // Graph launches run one ahead of the host: while launch k+1 runs,
+        // the state copied back after launch k is inspected, so the GPU does
+        // not idle between launches.  A launch queued after the stop finds
+        // `done` set and returns at once (it changes nothing).
+        int queued = 0, head = 0;
+        while (!h->h_state->done) {
+            const int planned = h->h_state->iter + queued * m;   // if nothing stops
+            if (queued < 2 && h->opts.max_iters - planned >= m) {
+                const int slot = (head + queued) & 1;
+                FW_CUDA(cudaGraphLaunch(h->graph, h->stream));
+                FW_CUDA(cudaMemcpyAsync(h->h_ring + slot, h->st, sizeof(ProbState),
+                                        cudaMemcpyDeviceToHost, h->stream));
+                FW_CUDA(cudaEventRecord(h->ring_ev[slot], h->stream));
+                h->launches += graph_launches(m);
+                ++queued;
+                continue;
+            }
+            if (queued == 0) break;   // fewer than m iterations left: the tail below
+            FW_CUDA(cudaEventSynchronize(h->ring_ev[head]));
+            *h->h_state = h->h_ring[head];
+            head ^= 1;
+            --queued;
+        }
+        if (queued) FW_TRY(read_state(h));   // the launch queued after the stop
+    }
     while (!h->h_state->done) {
-        const int R = h->opts.refresh_every;
         if (R > 0 && h->h_state->iter - h->last_refresh >= R) FW_TRY(refresh_lu(h));
         const int remaining = h->opts.max_iters - h->h_state->iter;
         if (remaining >= m && h->graph) {
             FW_CUDA(cudaGraphLaunch(h->graph, h->stream));
             h->launches += graph_launches(m);
         } else {
-            // direct launches; the tail (< m iterations left) ends with one more
-            // pass pair whose stop test, at the iteration cap, ends the solve
+            // direct launches with the decisions fused as in the graph; the
+            // tail (< m iterations left) ends with one more pass pair whose
+            // stop test, at the iteration cap, ends the solve
             const int it = remaining >= m ? m : remaining + 1;
-            for (int i = 0; i < it; ++i) iteration(h);
-            h->launches += 3 * it;
+            for (int i = 0; i < it; ++i) {
+                h->ops->passA(h->pd, h->st, h->stream, i > 0 ? 1 : 0);
+                h->ops->passB(h->pd, h->st, h->stream);
+            }
+            h->ops->finish(h->pd, h->st, h->stream);
+            h->launches += 2 * it + 1;
             FW_TRY(launch_check("iteration kernels"));
         }
         FW_TRY(read_state(h));

@@ -413,9 +413,13 @@ fw_status restart_problem(Ops* ops, const ProbDesc& pd, ProbState* st, bool from
     const int nb = int((pd.n + kBlock - 1) / kBlock);
     double* opart = nullptr;
     FW_TRYS(t.get(&opart, 8 * size_t(nb)));
-    if (!from_current) ops->reinit(pd, s);
     FW_CUDA(cudaMemsetAsync(pd.acc, 0, 8 * size_t(kAccTotal), s));
-    ops->spmm(pd, pd.U, pd.LU, s);
+    if (from_current) {
+        ops->spmm(pd, pd.U, pd.LU, s);
+    } else {
+        ops->reinit(pd, s);
+        ops->spmm_hat(pd, pd.LU, s);
+    }
     ops->objective(pd, pd.LU, opart, s);
     k_state_init<<<1, kBlock, 0, s>>>(st, opart, nb);
     return launched("restart kernels");

@@ -374,6 +374,25 @@ def test_graph_launch_equals_stepwise(blobs2k):
     assert np.array_equal(U1, U2)
 
 
+@pytest.mark.parametrize("weights,laplacian", [("f32", "sym"), ("bf16", "sym"), ("f64", "comb")])
+def test_lu0_from_fidelity_bytes_equals_dense_spmm(weights, laplacian):
+    """Create and reset form L U_0 from the fidelity bytes (U_0 = U_hat: an
+    unlabelled neighbour adds w/K to every class, a labelled one w to its
+    class); a refresh recomputes L U with the dense SpMM of the stored U.  The
+    two must agree bit for bit, so G' read before and after is identical."""
+    g = W.blobs_knn(n=2531, K=7, seed=17, label_frac=0.04)
+    with B.Segmenter(g, weight_dtype=weights, laplacian=laplacian) as s:
+        G0, ch0, act0 = s.grad()
+        s.refresh()
+        G1, ch1, act1 = s.grad()
+        assert np.array_equal(G0, G1)
+        assert np.array_equal(ch0, ch1) and np.array_equal(act0, act1)
+        s.step(3)
+        s.reset()                                  # reinit + L U_hat again
+        G2, _, _ = s.grad()
+        assert np.array_equal(G0, G2)
+
+
 def _stepwise(g, **opts):
     with B.Segmenter(g, **opts) as s:
         st = None
