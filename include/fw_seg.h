@@ -125,7 +125,14 @@ fw_status fw_seg_create(fw_seg **out, int64_t n, const int32_t *row_ptr_host,
 /* Run GFW iterations (Alg. 3) until the stop rule holds: no active row or
  * g_k <= 0 (stationary, FW_OK), g_k <= tolerance (FW_OK), or max_iters updates
  * (FW_NOT_CONVERGED).  The test is made before the update, as in step 4 of
- * Alg. 3.  stats may be NULL.  Errors: FW_ERR_NUMERIC, FW_ERR_CUDA. */
+ * Alg. 3.  stats may be NULL.  Errors: FW_ERR_NUMERIC, FW_ERR_CUDA.
+ * Execution: iterations run as a CUDA graph of iters_per_launch iterations
+ * (2 kernels each, the step decision of each iteration taken at the start of
+ * the next one, one finishing kernel per graph), launched repeatedly with one
+ * launch queued ahead of the host's state check; fewer than iters_per_launch
+ * remaining iterations run as direct launches of the same kernels.  With
+ * refresh_every > 0, or on a stream that cannot be captured, the host checks
+ * the state after every launch.  The stream is synchronised on return. */
 fw_status fw_seg_solve(fw_seg *h, fw_seg_stats *stats);
 
 /* Run at most `iters` iterations (fewer if the stop rule holds first) and
