@@ -289,6 +289,9 @@ template <typename WT, typename T>
 __global__ void k_build(int64_t n, const int32_t* rp, const int32_t* col, const double* w,
                         const double* deg, const int32_t* rpp, int32_t* colp, WT* valp, T* diag,
                         int comb) {
+    // deg holds d_i for L = D - W and d_i^{-1/2} for L_s (k_inv_sqrt): the
+    // normalised weight is then two FP64 products per entry, since FP64
+    // square roots and divisions per entry dominated this kernel on GB300
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int e0 = rp[i], e1 = rp[i + 1];
@@ -297,7 +300,7 @@ __global__ void k_build(int64_t n, const int32_t* rp, const int32_t* col, const 
     const double di = deg[i];
     for (int e = e0; e < e1; ++e, ++p) {
         const int j = col[e];
-        const double x = comb ? w[e] : w[e] / sqrt(di * deg[j]);
+        const double x = comb ? w[e] : (w[e] * di) * deg[j];
         colp[p] = j;
         if constexpr (sizeof(WT) == 2)
             valp[p] = __float2bfloat16_rn(__double2float_rn(x));

@@ -158,6 +158,13 @@ __global__ void k_pad_scan_add(int64_t n, const int32_t* __restrict__ bsum, int3
     if (i < n) out[i] += bsum[i / kScanRows];
 }
 
+// d_i <- 1 / sqrt(d_i) in place (FP64), so that k_build forms
+// W_hat_ij = w_ij d_i^{-1/2} d_j^{-1/2} with two products per entry.
+__global__ void k_inv_sqrt(int64_t n, double* deg) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) deg[i] = 1.0 / sqrt(deg[i]);
+}
+
 __global__ void k_fid(int64_t n, const int32_t* labels, int8_t* fid) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n) fid[i] = int8_t(labels[i]);
@@ -474,6 +481,7 @@ fw_status assemble_problem(Ops* ops, const HostGraph& g, const ProbLayout& lay, 
         set_error("graph: a node has degree 0");
         return FW_ERR_ISOLATED;
     }
+    if (!pd.comb) k_inv_sqrt<<<gr, kBlock, 0, s>>>(n, d_deg);
     ops->build(n, d_rp, d_col, d_w, d_deg, pd.rp, const_cast<int32_t*>(pd.col),
                const_cast<void*>(pd.val), const_cast<void*>(pd.diag), pd.comb, s);
     k_fid<<<gr, kBlock, 0, s>>>(n, d_lab, const_cast<int8_t*>(pd.fid));
