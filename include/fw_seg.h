@@ -198,6 +198,10 @@ fw_status fw_seg_profile(fw_seg *h, int32_t iters, double *ms_row_pass, double *
 /* Statistics of the handle's current state. */
 fw_status fw_seg_get_stats(fw_seg *h, fw_seg_stats *stats);
 
+/* Release the handle (NULL is a no-op).  Waits for the handle's stream; the
+ * device arrays go back, stream-ordered, to the library's per-device memory
+ * pool, which keeps up to 4 GiB of freed memory mapped so that a later create
+ * maps nothing new (create / destroy per request stays cheap). */
 void fw_seg_destroy(fw_seg *h);
 
 /* ------------------------------------------------------------------------

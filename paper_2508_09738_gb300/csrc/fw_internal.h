@@ -95,8 +95,12 @@ size_t problem_bytes(const ProbLayout& lay, size_t te, size_t we, bool comb);
 // Carve the problem's arrays out of [base, base + problem_bytes) and fill pd.
 void place_problem(char* base, const ProbLayout& lay, size_t te, size_t we, const fw_seg_opts& o,
                    ProbDesc& pd);
+// Stream-ordered device allocation from the library's per-device pool (freed
+// with cudaFreeAsync on a stream ordered after every use).  FW_ERR_NO_MEMORY
+// with the message set on failure.
+fw_status pool_alloc(void** out, size_t bytes, cudaStream_t s);
 // Upload, validate and build the problem into pd's arrays; U_0, L U_0 and the
-// fresh state *st.  Temporaries are stream-ordered (cudaMallocAsync).  Waits
+// fresh state *st.  Temporaries are stream-ordered (pool_alloc).  Waits
 // for the validation result on `s`.
 fw_status assemble_problem(Ops* ops, const HostGraph& g, const ProbLayout& lay, const ProbDesc& pd,
                            ProbState* st, cudaStream_t s);

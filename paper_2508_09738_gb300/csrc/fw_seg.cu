@@ -66,16 +66,13 @@ struct fw_seg {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::vector<void*> dev_allocs;
 
+    // device arrays: stream-ordered on the handle's stream, from the
+    // library's pool (fast to re-create after a destroy)
     template <typename P>
     fw_status alloc(P** p, size_t bytes) {
         void* q = nullptr;
-        cudaError_t e = cudaMalloc(&q, std::max<size_t>(bytes, 16));
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            set_error(std::string("cudaMalloc of ") + std::to_string(bytes) + " bytes failed: " +
-                      cudaGetErrorString(e));
-            return FW_ERR_NO_MEMORY;
-        }
+        const fw_status st = pool_alloc(&q, bytes, stream);
+        if (st != FW_OK) return st;
         dev_allocs.push_back(q);
         *p = reinterpret_cast<P*>(q);
         return FW_OK;
@@ -83,7 +80,7 @@ struct fw_seg {
     ~fw_seg() {
         if (stream) cudaStreamSynchronize(stream);
         if (graph) cudaGraphExecDestroy(graph);
-        for (void* p : dev_allocs) cudaFree(p);
+        for (void* p : dev_allocs) cudaFreeAsync(p, stream);   // back to the pool
         if (h_state) cudaFreeHost(h_state);
         if (h_ring) cudaFreeHost(h_ring);
         for (cudaEvent_t e : ring_ev)

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <mutex>
 #include <system_error>
 #include <thread>
 #include <vector>
@@ -386,6 +387,60 @@ void place_problem(char* base, const ProbLayout& lay, size_t te, size_t we, cons
     } while (0)
 
 // Stream-ordered temporaries, freed on every exit path.
+// ------------------------------------------------------------- memory
+// Handle arrays and create-time temporaries come from one stream-ordered
+// memory pool per device.  Unlike the device's default pool, which gives
+// freed memory back at every synchronisation, it keeps up to kPoolKeepBytes
+// of freed memory mapped, so repeated create / destroy cycles (a request
+// stream, the end-to-end loop) map no new memory.
+constexpr uint64_t kPoolKeepBytes = 4ull << 30;
+constexpr int kPoolMaxDevices = 64;
+
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pools[kPoolMaxDevices] = {};
+
+static cudaError_t device_pool(cudaMemPool_t* out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kPoolMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (!g_pools[dev]) {
+        cudaMemPoolProps props;
+        std::memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t p = nullptr;
+        e = cudaMemPoolCreate(&p, &props);
+        if (e != cudaSuccess) return e;
+        uint64_t keep = kPoolKeepBytes;
+        e = cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (e != cudaSuccess) {
+            cudaMemPoolDestroy(p);
+            return e;
+        }
+        g_pools[dev] = p;
+    }
+    *out = g_pools[dev];
+    return cudaSuccess;
+}
+
+fw_status pool_alloc(void** out, size_t bytes, cudaStream_t s) {
+    *out = nullptr;
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = device_pool(&pool);
+    if (e == cudaSuccess) e = cudaMallocFromPoolAsync(out, std::max<size_t>(bytes, 16), pool, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *out = nullptr;
+        set_error(std::string("device allocation of ") + std::to_string(bytes) +
+                  " bytes failed: " + cudaGetErrorString(e));
+        return FW_ERR_NO_MEMORY;
+    }
+    return FW_OK;
+}
+
 struct Temps {
     cudaStream_t s;
     std::vector<void*> ptrs;
@@ -396,13 +451,8 @@ struct Temps {
     template <typename P>
     fw_status get(P** out, size_t bytes) {
         void* q = nullptr;
-        cudaError_t e = cudaMallocAsync(&q, std::max<size_t>(bytes, 16), s);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            set_error(std::string("cudaMallocAsync of ") + std::to_string(bytes) +
-                      " bytes failed: " + cudaGetErrorString(e));
-            return FW_ERR_NO_MEMORY;
-        }
+        const fw_status st = pool_alloc(&q, bytes, s);
+        if (st != FW_OK) return st;
         ptrs.push_back(q);
         *out = reinterpret_cast<P*>(q);
         return FW_OK;
