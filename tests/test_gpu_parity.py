@@ -393,6 +393,28 @@ def test_lu0_from_fidelity_bytes_equals_dense_spmm(weights, laplacian):
         assert np.array_equal(G0, G2)
 
 
+def test_create_destroy_reuse_pooled_memory():
+    """Handles take their arrays from a per-device pool that keeps freed memory
+    mapped, so later handles get recycled (non-zero) memory.  Interleaved
+    sizes and repeated create/solve/destroy must give the same bits every
+    time (nothing may rely on fresh memory being zero)."""
+    gs = [W.blobs_knn(n=1537, K=7, seed=5), W.sbm(n=20_000, K=10, deg_in=20.0, deg_out=2.0,
+                                                 label_frac=0.01, seed=4)]
+    first = {}
+    for rep in range(4):
+        for i, g in enumerate(gs if rep % 2 == 0 else gs[::-1]):
+            key = g.n
+            with B.Segmenter(g, weight_dtype="f32", max_iters=40, iters_per_launch=16) as s:
+                st = s.solve()
+                out = (s.U(), s.labels(), st.iters, st.gap, st.objective)
+            if key not in first:
+                first[key] = out
+            else:
+                ref = first[key]
+                assert np.array_equal(out[0], ref[0]) and np.array_equal(out[1], ref[1])
+                assert out[2:] == ref[2:]
+
+
 def _stepwise(g, **opts):
     with B.Segmenter(g, **opts) as s:
         st = None
