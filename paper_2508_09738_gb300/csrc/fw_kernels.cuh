@@ -223,22 +223,24 @@ __global__ void k_labels(ProbDesc pd, int32_t* out) {
 // (eq. gradgl_vv2): 1/2 <U, L U> + 1/eps sum u(1-u) + 1/2 sum w_i ||u_hat_i - u_i||^2.
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_objective(ProbDesc pd, const T* LUf, double* part) {
+    // per row in the iterate type (FP64 per element was the bulk of this
+    // kernel on GB300), across rows in FP64
     const int r = blockIdx.x * kBlock + threadIdx.x;
     double e = 0.0;
     if (r < pd.n) {
         const T* Ub = static_cast<const T*>(pd.U);
         const int f = pd.fid[r];
-        double quad = 0.0, pen = 0.0, fidt = 0.0;
+        T quad = T(0), pen = T(0), fidt = T(0);
         for (int k = 0; k < pd.K; ++k) {
-            const double u = double(Ub[(int64_t)k * pd.npad + r]);
-            quad += u * double(LUf[(int64_t)k * pd.npad + r]);
-            pen += u * (1.0 - u);
+            const T u = Ub[(int64_t)k * pd.npad + r];
+            quad = fma_(u, LUf[(int64_t)k * pd.npad + r], quad);
+            pen = fma_(u, sub_(T(1), u), pen);
             if (f >= 0) {
-                const double d = (k == f ? 1.0 : 0.0) - u;
-                fidt += d * d;
+                const T d = sub_(k == f ? T(1) : T(0), u);
+                fidt = fma_(d, d, fidt);
             }
         }
-        e = 0.5 * quad + pd.inv_eps * pen + 0.5 * pd.omega0 * fidt;
+        e = 0.5 * double(quad) + pd.inv_eps * double(pen) + 0.5 * pd.omega0 * double(fidt);
     }
     const double v[1] = {e};
     block_partials<double, 1>(v, part + blockIdx.x);
