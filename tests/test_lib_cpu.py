@@ -122,3 +122,23 @@ def test_product_code_never_imports_oracle():
                         assert not (node.module or "").startswith("oracle"), p
             if f.endswith((".cu", ".cuh", ".h", ".cpp")):
                 assert "oracle/" not in open(p).read(), p
+
+
+@pytest.mark.parametrize("name", ["blobs2k", "sbm200k"])
+def test_product_form_weights_round_like_the_oracle(name):
+    """The build kernel forms W_hat_ij as (w_ij * d_i^-1/2) * d_j^-1/2 with
+    d_i^-1/2 = 1 / sqrt(d_i), all IEEE FP64 operations (so numpy reproduces
+    them exactly); the oracle forms w_ij / sqrt(d_i d_j).  The FP64 values
+    differ by a few ulp, and the stored FP32 / BF16 weights must not."""
+    import numpy as np
+    import oracle.gfw as O
+    from paper_2508_09738_gb300 import workloads as W
+    g = W.make_config_graph(name)
+    d = O.degrees(g.n, g.row_ptr, g.col, g.w)
+    ref = O.normalized_weights(g.n, g.row_ptr, g.col, g.w)
+    rows = np.repeat(np.arange(g.n), np.diff(g.row_ptr))
+    s = 1.0 / np.sqrt(d)
+    prod = (g.w * s[rows]) * s[g.col]
+    assert np.max(np.abs(prod - ref) / np.spacing(ref)) <= 8
+    for dt in ("f32", "bf16"):
+        assert np.array_equal(O.round_weights(prod, dt), O.round_weights(ref, dt))
