@@ -4,6 +4,7 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -99,11 +100,47 @@ void place_problem(char* base, const ProbLayout& lay, size_t te, size_t we, cons
 // with cudaFreeAsync on a stream ordered after every use).  FW_ERR_NO_MEMORY
 // with the message set on failure.
 fw_status pool_alloc(void** out, size_t bytes, cudaStream_t s);
+
+// Stream-ordered temporaries, released (stream-ordered) when the object dies.
+struct Temps {
+    cudaStream_t s;
+    std::vector<void*> ptrs;
+    explicit Temps(cudaStream_t st) : s(st) {}
+    ~Temps() {
+        for (void* p : ptrs) cudaFreeAsync(p, s);
+    }
+    template <typename P>
+    fw_status get(P** out, size_t bytes) {
+        void* q = nullptr;
+        const fw_status st = pool_alloc(&q, bytes, s);
+        if (st != FW_OK) return st;
+        ptrs.push_back(q);
+        *out = reinterpret_cast<P*>(q);
+        return FW_OK;
+    }
+};
+
+// Device copies of a caller's input arrays (row_ptr, col, w, labels).
+struct Upload {
+    Temps t;
+    int64_t n = 0, nnz = 0;
+    int32_t *rp = nullptr, *col = nullptr, *lab = nullptr;
+    double* w = nullptr;
+    explicit Upload(cudaStream_t s) : t(s) {}
+};
+// The O(1) checks the upload relies on: n, pointers, row_ptr[0] and nnz.
+fw_status check_graph_args(const HostGraph& g);
+// Enqueue the copies of g's arrays on up's stream (asynchronous from pinned
+// host memory; the caller's arrays must stay valid until the stream passes).
+fw_status upload_inputs(const HostGraph& g, Upload& up);
 // Upload, validate and build the problem into pd's arrays; U_0, L U_0 and the
 // fresh state *st.  Temporaries are stream-ordered (pool_alloc).  Waits
 // for the validation result on `s`.
 fw_status assemble_problem(Ops* ops, const HostGraph& g, const ProbLayout& lay, const ProbDesc& pd,
                            ProbState* st, cudaStream_t s);
+// The same from inputs already uploaded (or in flight) on stream s.
+fw_status assemble_uploaded(Ops* ops, Upload& up, const ProbLayout& lay, const ProbDesc& pd,
+                            ProbState* st, cudaStream_t s);
 // Restart pd at U_0 (or at its current U when from_current) with a fresh state.
 fw_status restart_problem(Ops* ops, const ProbDesc& pd, ProbState* st, bool from_current,
                           cudaStream_t s);

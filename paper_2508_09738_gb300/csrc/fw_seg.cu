@@ -52,8 +52,8 @@ struct fw_seg {
     std::unique_ptr<Ops> ops;
     ProbDesc pd{};
     ProbState* st = nullptr;        // device
-    ProbState* h_state = nullptr;   // pinned mirror
-    ProbState* h_ring = nullptr;    // pinned [2]: state copies of queued graph launches
+    ProbState* h_state = nullptr;   // pinned mirror (start of one pinned block of three)
+    ProbState* h_ring = nullptr;    // h_state + 1, [2]: state copies of queued graph launches
     cudaEvent_t ring_ev[2] = {nullptr, nullptr};
     char* mem = nullptr;            // the problem's arrays
     void* d_tmp = nullptr;          // T[K][npad]: fresh L U, gradient
@@ -81,8 +81,7 @@ struct fw_seg {
         if (stream) cudaStreamSynchronize(stream);
         if (graph) cudaGraphExecDestroy(graph);
         for (void* p : dev_allocs) cudaFreeAsync(p, stream);   // back to the pool
-        if (h_state) cudaFreeHost(h_state);
-        if (h_ring) cudaFreeHost(h_ring);
+        if (h_state) cudaFreeHost(h_state);   // h_ring lives in the same block
         for (cudaEvent_t e : ring_ev)
             if (e) cudaEventDestroy(e);
         if (ev0) cudaEventDestroy(ev0);
@@ -265,8 +264,13 @@ fw_status fw_seg_create(fw_seg** out, int64_t n, const int32_t* row_ptr, const i
         FW_TRY(check_opts(o));
         const HostGraph g{n, row_ptr, col, w, K, labels};
         std::unique_ptr<fw_seg> h(new fw_seg());
-        FW_TRY(plan_problem(g, o, h->lay));
-        h->lay.cls4 = K <= 16;   // pass B gathers 4-bit classes (KMAX <= 16 forms)
+        // Large inputs start their upload before the host's planning pass
+        // over row_ptr and labels, which then runs while the copies are in
+        // flight.  On every error path the handle's destructor waits for its
+        // stream, so the caller's arrays are not read after the call returns.
+        const bool upload_first = n >= (int64_t(1) << 20);
+        if (upload_first) FW_TRY(check_graph_args(g));
+        else FW_TRY(plan_problem(g, o, h->lay));
         FW_CUDA(cudaGetDevice(&h->device));
         h->opts = o;
         if (o.cuda_stream) {
@@ -275,11 +279,15 @@ fw_status fw_seg_create(fw_seg** out, int64_t n, const int32_t* row_ptr, const i
             FW_CUDA(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
             h->own_stream = true;
         }
+        Upload up(h->stream);
+        FW_TRY(upload_inputs(g, up));
+        if (upload_first) FW_TRY(plan_problem(g, o, h->lay));
+        h->lay.cls4 = K <= 16;   // pass B gathers 4-bit classes (KMAX <= 16 forms)
         h->ops.reset(make_ops(o.weight_dtype, K));
         if (!h->ops) return invalid("no kernels for this weight dtype / K");
         FW_CUDA(h->ops->configure());
-        FW_CUDA(cudaMallocHost(&h->h_state, sizeof(ProbState)));
-        FW_CUDA(cudaMallocHost(&h->h_ring, 2 * sizeof(ProbState)));
+        FW_CUDA(cudaMallocHost(&h->h_state, 3 * sizeof(ProbState)));
+        h->h_ring = h->h_state + 1;
         for (cudaEvent_t& e : h->ring_ev)
             FW_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         FW_CUDA(cudaEventCreate(&h->ev0));
@@ -294,7 +302,7 @@ fw_status fw_seg_create(fw_seg** out, int64_t n, const int32_t* row_ptr, const i
         FW_TRY(h->alloc(&h->d_ch, size_t(lay.n)));
         FW_TRY(h->alloc(&h->d_labels, 4 * size_t(lay.n)));
         FW_TRY(h->alloc(&h->d_opart, 8 * size_t((lay.n + kBlock - 1) / kBlock)));
-        FW_TRY(assemble_problem(h->ops.get(), g, lay, h->pd, h->st, h->stream));
+        FW_TRY(assemble_uploaded(h->ops.get(), up, lay, h->pd, h->st, h->stream));
         FW_TRY(read_state(h.get()));
         if (build_graph(h.get()) != FW_OK) {
             // streams that cannot be captured (the legacy default stream) run

@@ -386,7 +386,6 @@ void place_problem(char* base, const ProbLayout& lay, size_t te, size_t we, cons
         if (s_ != FW_OK) return s_;     \
     } while (0)
 
-// Stream-ordered temporaries, freed on every exit path.
 // ------------------------------------------------------------- memory
 // Handle arrays and create-time temporaries come from one stream-ordered
 // memory pool per device.  Unlike the device's default pool, which gives
@@ -441,23 +440,6 @@ fw_status pool_alloc(void** out, size_t bytes, cudaStream_t s) {
     return FW_OK;
 }
 
-struct Temps {
-    cudaStream_t s;
-    std::vector<void*> ptrs;
-    explicit Temps(cudaStream_t st) : s(st) {}
-    ~Temps() {
-        for (void* p : ptrs) cudaFreeAsync(p, s);
-    }
-    template <typename P>
-    fw_status get(P** out, size_t bytes) {
-        void* q = nullptr;
-        const fw_status st = pool_alloc(&q, bytes, s);
-        if (st != FW_OK) return st;
-        ptrs.push_back(q);
-        *out = reinterpret_cast<P*>(q);
-        return FW_OK;
-    }
-};
 
 static fw_status launched(const char* what) {
     cudaError_t e = cudaGetLastError();
@@ -482,26 +464,60 @@ fw_status restart_problem(Ops* ops, const ProbDesc& pd, ProbState* st, bool from
     return launched("restart kernels");
 }
 
+fw_status check_graph_args(const HostGraph& g) {
+    if (g.n < 1 || g.n >= (int64_t(1) << 31) - 1) return invalid("n must be in [1, 2^31-1)");
+    if (!g.rp || !g.labels) return invalid("row_ptr and labels must not be NULL");
+    if (g.rp[0] != 0) {
+        set_error("row_ptr[0] must be 0");
+        return FW_ERR_GRAPH;
+    }
+    if (g.rp[g.n] < 0) {
+        set_error("row_ptr[n] must be >= 0");
+        return FW_ERR_GRAPH;
+    }
+    if (g.rp[g.n] > 0 && (!g.col || !g.w)) return invalid("col and w must not be NULL");
+    return FW_OK;
+}
+
+fw_status upload_inputs(const HostGraph& g, Upload& up) {
+    const cudaStream_t s = up.t.s;
+    const int64_t n = g.n, nnz = g.rp[g.n];
+    up.n = n;
+    up.nnz = nnz;
+    FW_TRYS(up.t.get(&up.rp, 4 * (size_t(n) + 1)));
+    FW_TRYS(up.t.get(&up.col, 4 * size_t(nnz)));
+    FW_TRYS(up.t.get(&up.w, 8 * size_t(nnz)));
+    FW_TRYS(up.t.get(&up.lab, 4 * size_t(n)));
+    FW_CUDA(cudaMemcpyAsync(up.rp, g.rp, 4 * (size_t(n) + 1), cudaMemcpyHostToDevice, s));
+    if (nnz) {
+        FW_CUDA(cudaMemcpyAsync(up.col, g.col, 4 * size_t(nnz), cudaMemcpyHostToDevice, s));
+        FW_CUDA(cudaMemcpyAsync(up.w, g.w, 8 * size_t(nnz), cudaMemcpyHostToDevice, s));
+    }
+    FW_CUDA(cudaMemcpyAsync(up.lab, g.labels, 4 * size_t(n), cudaMemcpyHostToDevice, s));
+    return FW_OK;
+}
+
 fw_status assemble_problem(Ops* ops, const HostGraph& g, const ProbLayout& lay, const ProbDesc& pd,
                            ProbState* st, cudaStream_t s) {
-    Temps t(s);
-    const int64_t n = lay.n, nnz = lay.nnz;
+    Upload up(s);
+    FW_TRYS(check_graph_args(g));
+    FW_TRYS(upload_inputs(g, up));
+    return assemble_uploaded(ops, up, lay, pd, st, s);
+}
+
+fw_status assemble_uploaded(Ops* ops, Upload& up, const ProbLayout& lay, const ProbDesc& pd,
+                            ProbState* st, cudaStream_t s) {
+    Temps& t = up.t;
+    const int64_t n = lay.n;
     const size_t te = ops->elem();
-    int32_t *d_rp = nullptr, *d_col = nullptr, *d_lab = nullptr;
-    double *d_w = nullptr, *d_deg = nullptr;
+    const int32_t* d_rp = up.rp;
+    const int32_t* d_col = up.col;
+    const double* d_w = up.w;
+    const int32_t* d_lab = up.lab;
+    double* d_deg = nullptr;
     int* d_err = nullptr;
-    FW_TRYS(t.get(&d_rp, 4 * (size_t(n) + 1)));
-    FW_TRYS(t.get(&d_col, 4 * size_t(nnz)));
-    FW_TRYS(t.get(&d_w, 8 * size_t(nnz)));
     FW_TRYS(t.get(&d_deg, 8 * size_t(n)));
-    FW_TRYS(t.get(&d_lab, 4 * size_t(n)));
     FW_TRYS(t.get(&d_err, sizeof(int)));
-    FW_CUDA(cudaMemcpyAsync(d_rp, g.rp, 4 * (size_t(n) + 1), cudaMemcpyHostToDevice, s));
-    if (nnz) {
-        FW_CUDA(cudaMemcpyAsync(d_col, g.col, 4 * size_t(nnz), cudaMemcpyHostToDevice, s));
-        FW_CUDA(cudaMemcpyAsync(d_w, g.w, 8 * size_t(nnz), cudaMemcpyHostToDevice, s));
-    }
-    FW_CUDA(cudaMemcpyAsync(d_lab, g.labels, 4 * size_t(n), cudaMemcpyHostToDevice, s));
     {   // padded row offsets into pd.rp
         const int nb = int((n + kScanRows - 1) / kScanRows);
         int32_t* d_bsum = nullptr;
