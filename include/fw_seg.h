@@ -186,14 +186,27 @@ fw_status fw_seg_refresh(fw_seg *h);
  * after fw_seg_create.  Used to time repeated solves of one resident graph. */
 fw_status fw_seg_reset(fw_seg *h);
 
-/* Measurement: run `iters` (1..4096) iterations as separate launches, enqueued
- * back to back on the handle's stream with a CUDA event between consecutive
- * kernels (one host wait at the end); the outputs (each nullable) get the mean
- * device time in milliseconds of pass A (update, gradient, GLMO, gap pieces),
- * pass B (one-hot L S, <D, L S>) and the finishing kernel (exact totals, stop
- * test, line search).  The iterate advances. */
+/* Measurement of the iteration kernels in the form fw_seg_solve runs them
+ * (each time is taken with two CUDA events on the handle's stream around one
+ * captured graph, so no event sits between kernels):
+ *   *ms_per_iter  a graph of `iters` (1..4096) fused iterations (pass A with
+ *                 the previous iteration's step decision, pass B) and one
+ *                 finishing kernel, divided by iters;
+ *   *ms_row_pass  a graph of `iters` launches of the fused pass A (update,
+ *                 step decision, gradient, GLMO, gap pieces), per launch;
+ *   *ms_csr_pass  a graph of `iters` launches of pass B (one-hot L S,
+ *                 <D, L S>), per launch;
+ *   *ms_finish    one finishing kernel (exact totals, stop test, line
+ *                 search), launched directly.
+ * The repeated passes run on a copy of the problem's mutable arrays taken
+ * before and put back after, so they do not change the iterate.  *in_graph
+ * is 1; on a stream that cannot be captured the same launches are enqueued
+ * directly and *in_graph is 0.  Outputs may be NULL.  The handle must not
+ * have stopped (reset first); afterwards the iterate has advanced by
+ * iters + 1 iterations, exactly as fw_seg_step(h, iters + 1) would have
+ * advanced it (FW_ERR_INVALID_ARG if the stop rule holds on the way). */
 fw_status fw_seg_profile(fw_seg *h, int32_t iters, double *ms_row_pass, double *ms_csr_pass,
-                         double *ms_finish);
+                         double *ms_finish, double *ms_per_iter, int32_t *in_graph);
 
 /* Statistics of the handle's current state. */
 fw_status fw_seg_get_stats(fw_seg *h, fw_seg_stats *stats);
@@ -339,9 +352,11 @@ void fw_srv_destroy(fw_srv *s);
  * Allocation-free energy evaluation.
  *
  * The paper has no counterpart to this call: it is a service entry point.  It
- * evaluates the objective E(U) of Sec. 2.1 (the energy of eq. gradgl_vv2,
- * as fw_seg_objective does for a handle) for a graph and an iterate that are
- * already in the caller's device memory, without allocating device memory.
+ * evaluates the objective E(U) = 1/2 <U, L U> (the Laplacian quadratic form)
+ * + (1/eps) sum u (1 - u) (the penalty) + 1/2 sum_i omega_i ||u_hat_i - u_i||^2
+ * (the fidelity term), the value fw_seg_objective gives for a handle, for a
+ * graph and an iterate that are already in the caller's device memory,
+ * without allocating device memory.
  * It is meant for callers that cannot allocate: a process whose device memory
  * is held by another allocator (cudaMalloc would fail), or a loop that must
  * not call cudaMalloc / cudaFree (they may synchronise the device).  Its
@@ -370,7 +385,9 @@ void fw_srv_destroy(fw_srv *s);
  * energy; FW_ERR_CUDA.  Symmetry of W is not checked.
  * The first call on each device looks up the scratch array's address
  * (cudaGetSymbolAddress, which may load the module's device data) and caches
- * it; make that first call before any stream capture.  All calls on a device
+ * it with the identity of the current CUDA context; a call in a new context
+ * of the device (after cudaDeviceReset, say) looks it up again.  Make the
+ * first call on a device before any stream capture.  All calls on a device
  * share its one scratch array: calls that overlap in time on the same device
  * race and may return wrong values, so the caller serialises them.
  * ---------------------------------------------------------------------- */

@@ -113,7 +113,7 @@ _SIGS = {
     "fw_seg_get_stats": (c_int32, [c_void_p, POINTER(fw_seg_stats)]),
     "fw_seg_reset": (c_int32, [c_void_p]),
     "fw_seg_profile": (c_int32, [c_void_p, c_int32, POINTER(c_double), POINTER(c_double),
-                                 POINTER(c_double)]),
+                                 POINTER(c_double), POINTER(c_double), POINTER(c_int32)]),
     "fw_seg_destroy": (None, [c_void_p]),
     "fw_batch_default_opts": (c_int32, [POINTER(fw_batch_opts)]),
     "fw_batch_create": (c_int32, [POINTER(c_void_p), c_int32, POINTER(fw_graph),
@@ -292,12 +292,18 @@ def fw_seg_reset(h: Handle) -> None:
     _check(lib().fw_seg_reset(h.ptr))
 
 
-def fw_seg_profile(h: Handle, iters: int):
-    """Mean device ms of (pass A, pass B, finish) over `iters` separately launched iterations."""
-    a, b, f = c_double(), c_double(), c_double()
+def fw_seg_profile(h: Handle, iters: int) -> dict:
+    """Device ms of the iteration kernels as the solve runs them: per
+    iteration of a graph of `iters` fused iterations (per_iter), per launch of
+    graphs of `iters` back-to-back launches of pass A (pass_a) and of pass B
+    (pass_b), and one finishing kernel (finish); in_graph = 0 when the stream
+    could not be captured.  The iterate advances by iters + 1 iterations."""
+    a, b, f, t = c_double(), c_double(), c_double(), c_double()
+    g = c_int32()
     _check(lib().fw_seg_profile(h.ptr, int(iters), ctypes.byref(a), ctypes.byref(b),
-                                ctypes.byref(f)))
-    return a.value, b.value, f.value
+                                ctypes.byref(f), ctypes.byref(t), ctypes.byref(g)))
+    return dict(pass_a=a.value, pass_b=b.value, finish=f.value, per_iter=t.value,
+                in_graph=int(g.value))
 
 
 def fw_seg_destroy(h: Handle) -> None:

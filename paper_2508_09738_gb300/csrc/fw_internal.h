@@ -128,7 +128,7 @@ struct Upload {
     double* w = nullptr;
     explicit Upload(cudaStream_t s) : t(s) {}
 };
-// The O(1) checks the upload relies on: n, pointers, row_ptr[0] and nnz.
+// The O(1) checks the upload relies on: n, K, pointers, row_ptr[0] and nnz.
 fw_status check_graph_args(const HostGraph& g);
 // Enqueue the copies of g's arrays on up's stream (asynchronous from pinned
 // host memory; the caller's arrays must stay valid until the stream passes).

@@ -1,6 +1,9 @@
-// fw_energy_noalloc: the objective E(U) (Sec. 2.1, eq. gradgl_vv2's energy)
-// of a graph and an iterate that live in the caller's device memory, with no
-// device allocation by the call.
+// fw_energy_noalloc: the objective E(U) -- the Laplacian quadratic form
+// 1/2 <U, L U>, plus the penalty (1/eps) sum u (1 - u), plus the fidelity
+// term 1/2 sum_i omega_i ||u_hat_i - u_i||^2 -- of a graph and an iterate
+// that live in the caller's device memory, with no device allocation by the
+// call.  The paper has no counterpart to this entry point: it is a service
+// of the library.
 //
 // This is the allocation-free variant of the handle's objective evaluation
 // (k_objective, which takes its fresh L U product and its partial sums from
@@ -17,12 +20,15 @@
 //
 // Set-up: the first call on each device, with that device current, looks the
 // scratch array up with cudaGetSymbolAddress (which may load the module's
-// device data) and caches the address.  Make that first call before any
-// stream capture.
+// device data) and caches the address together with the identity of the
+// current CUDA context.  A later call in another context of that device (for
+// instance after cudaDeviceReset) looks the address up again.  Make the first
+// call on a device before any stream capture.
 //
 // Calls share the one scratch array of their device: two calls that overlap
 // in time on the same device (from two host threads, or on two streams
 // without an ordering between them) race on it and may return wrong values.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -125,9 +131,44 @@ k_na_energy(int64_t n, int64_t nnz, int K, const int32_t* __restrict__ rp,
 }
 
 std::mutex g_na_mu;
-void* g_na_ptr[kNaMaxDevices] = {};
+struct NaCache {
+    unsigned long long ctx = 0;   // unique id of the context the address belongs to
+    void* ptr = nullptr;
+};
+NaCache g_na_cache[kNaMaxDevices];
 
-// Device address of this device's scratch array (looked up once per device).
+// Unique id of the current CUDA context (the driver's cuCtxGetCurrent and
+// cuCtxGetId, reached through the runtime's entry-point query, so the library
+// needs no link against the driver library).  0 when it cannot be read: the
+// caller then looks the address up on every call.
+unsigned long long current_ctx_id() {
+    typedef CUresult (*get_current_fn)(CUcontext*);
+    typedef CUresult (*get_id_fn)(CUcontext, unsigned long long*);
+    static get_current_fn get_current = nullptr;
+    static get_id_fn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 4000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<get_current_fn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<get_id_fn>(f);
+        cudaGetLastError();
+    });
+    if (!get_current || !get_id) return 0;
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&c) != CUDA_SUCCESS || !c) return 0;
+    if (get_id(c, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+// Device address of this device's scratch array, looked up once per device
+// and context.
 fw_status na_scratch(void** out) {
     int dev = 0;
     FW_CUDA(cudaGetDevice(&dev));
@@ -135,14 +176,19 @@ fw_status na_scratch(void** out) {
         set_error("fw_energy_noalloc: device ordinal out of the supported range");
         return FW_ERR_UNSUPPORTED;
     }
+    // before the process's first CUDA work no context is current yet (id 0):
+    // the lookup below then creates it, and the next call caches its id
+    const unsigned long long ctx = current_ctx_id();
     std::lock_guard<std::mutex> lock(g_na_mu);
-    if (!g_na_ptr[dev]) {
+    NaCache& c = g_na_cache[dev];
+    if (!c.ptr || ctx == 0 || c.ctx != ctx) {
         void* p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
-        g_na_ptr[dev] = p;
+        c.ptr = p;
+        c.ctx = ctx;
     }
-    *out = g_na_ptr[dev];
+    *out = c.ptr;
     return FW_OK;
 }
 

@@ -210,6 +210,89 @@ static fw_status copy_soa_to_host(fw_seg* h, const void* dev, double* out) {
     return FW_OK;
 }
 
+// ---------------------------------------------------------------- profile
+// Everything a pass may change, copied aside so that timing runs of repeated
+// passes leave the iterate as it was.
+struct Snapshot {
+    void *U = nullptr, *LU = nullptr, *LS = nullptr, *ch = nullptr, *c4 = nullptr;
+    void *acc = nullptr, *st = nullptr;
+};
+
+static fw_status copy_problem_state(fw_seg* h, const Snapshot& s, bool save) {
+    const size_t blk = h->ops->elem() * size_t(h->lay.npad) * size_t(h->lay.K);
+    const size_t n = size_t(h->lay.n);
+    struct Piece {
+        void* dev;
+        void* keep;
+        size_t bytes;
+    } pieces[] = {{h->pd.U, s.U, blk},
+                  {h->pd.LU, s.LU, blk},
+                  {h->pd.LS, s.LS, blk},
+                  {h->pd.choice, s.ch, n},
+                  {h->pd.cls4, s.c4, h->pd.cls4 ? (n + 1) / 2 : 0},
+                  {h->pd.acc, s.acc, 8 * size_t(kAccTotal)},
+                  {h->st, s.st, sizeof(ProbState)}};
+    for (const Piece& p : pieces) {
+        if (!p.bytes) continue;
+        FW_CUDA(cudaMemcpyAsync(save ? p.keep : p.dev, save ? p.dev : p.keep, p.bytes,
+                                cudaMemcpyDeviceToDevice, h->stream));
+    }
+    return FW_OK;
+}
+
+// Enqueue `body` once, as a captured graph when the stream can be captured
+// (else directly), between two events recorded on the stream around it;
+// *ms = the elapsed time.  The graph is uploaded before the first event so
+// that the time is its execution only.
+template <typename Body>
+static fw_status time_enqueued(fw_seg* h, bool graph, Body body, cudaEvent_t e0, cudaEvent_t e1,
+                               float* ms) {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    if (graph) {
+        FW_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+        body();
+        cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+        if (e == cudaSuccess) e = cudaGraphUpload(ge, h->stream);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            if (ge) cudaGraphExecDestroy(ge);
+            return cuda_fail(e, "profile graph");
+        }
+    }
+    FW_CUDA(cudaEventRecord(e0, h->stream));
+    if (graph) {
+        const cudaError_t e = cudaGraphLaunch(ge, h->stream);
+        if (e != cudaSuccess) {
+            cudaGraphExecDestroy(ge);
+            return cuda_fail(e, "cudaGraphLaunch");
+        }
+    } else {
+        body();
+    }
+    FW_CUDA(cudaEventRecord(e1, h->stream));
+    FW_CUDA(cudaEventSynchronize(e1));
+    if (ge) cudaGraphExecDestroy(ge);
+    FW_TRY(launch_check("profile kernels"));
+    FW_CUDA(cudaEventElapsedTime(ms, e0, e1));
+    return FW_OK;
+}
+
+// Whether the handle's stream can be captured (the legacy default stream
+// cannot); the capture error, if any, is cleared.
+static bool stream_capturable(fw_seg* h) {
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const bool ok = cudaStreamEndCapture(h->stream, &g) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return ok;
+}
+
 extern "C" {
 
 const char* fw_seg_last_error(void) { return last_error_text(); }
@@ -266,11 +349,18 @@ fw_status fw_seg_create(fw_seg** out, int64_t n, const int32_t* row_ptr, const i
         std::unique_ptr<fw_seg> h(new fw_seg());
         // Large inputs start their upload before the host's planning pass
         // over row_ptr and labels, which then runs while the copies are in
-        // flight.  On every error path the handle's destructor waits for its
-        // stream, so the caller's arrays are not read after the call returns.
-        const bool upload_first = n >= (int64_t(1) << 20);
-        if (upload_first) FW_TRY(check_graph_args(g));
-        else FW_TRY(plan_problem(g, o, h->lay));
+        // flight.  The O(1) checks (n, K, pointers, row_ptr ends) come first,
+        // and so does the full planning pass whenever the padded entry count
+        // could reach the 2^31 limit, so that a size the library rejects never
+        // queues a copy.  On every error path the handle's destructor waits
+        // for its stream, so the caller's arrays are not read after the call
+        // returns.
+        bool upload_first = n >= (int64_t(1) << 20);
+        if (upload_first) {
+            FW_TRY(check_graph_args(g));
+            upload_first = int64_t(row_ptr[n]) + int64_t(kPadW - 1) * n < (int64_t(1) << 31);
+        }
+        if (!upload_first) FW_TRY(plan_problem(g, o, h->lay));
         FW_CUDA(cudaGetDevice(&h->device));
         h->opts = o;
         if (o.cuda_stream) {
@@ -388,51 +478,73 @@ fw_status fw_seg_reset(fw_seg* h) {
     return FW_OK;
 }
 
-fw_status fw_seg_profile(fw_seg* h, int32_t iters, double* ms_a, double* ms_b, double* ms_f) {
+fw_status fw_seg_profile(fw_seg* h, int32_t iters, double* ms_a, double* ms_b, double* ms_f,
+                         double* ms_iter, int32_t* in_graph) {
     if (!h || iters < 1 || iters > 4096) return invalid("bad arguments (iters in [1, 4096])");
-    // all iterations are enqueued back to back with an event between
-    // consecutive kernels, and the host waits once at the end, so each interval
-    // is the kernel's time in a busy stream (no per-launch idle gap)
-    std::vector<cudaEvent_t> ev(3 * size_t(iters) + 1, nullptr);
-    fw_status rc = FW_OK;
-    for (auto& e : ev) {
-        const cudaError_t ce = cudaEventCreate(&e);
-        if (ce != cudaSuccess) {
-            rc = cuda_fail(ce, "cudaEventCreate");
-            break;
+    FW_TRY(read_state(h));
+    if (h->h_state->done) return invalid("the solve has stopped: reset before profiling");
+    const int m = iters;
+    const bool graph = stream_capturable(h);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    FW_CUDA(cudaEventCreate(&e0));
+    FW_CUDA(cudaEventCreate(&e1));
+    struct EvGuard {
+        cudaEvent_t a, b;
+        ~EvGuard() {
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
         }
-    }
-    if (rc == FW_OK) {
-        for (int i = 0; i < iters; ++i) {
-            cudaEventRecord(ev[3 * i], h->stream);
-            h->ops->passA(h->pd, h->st, h->stream, 0);
-            cudaEventRecord(ev[3 * i + 1], h->stream);
+    } guard{e0, e1};
+    // 1. the solve's own form: m fused iterations and one finish
+    float t_ab = 0.f, t_a = 0.f, t_b = 0.f, t_f = 0.f;
+    FW_TRY(time_enqueued(h, graph, [&] {
+        for (int i = 0; i < m; ++i) {
+            h->ops->passA(h->pd, h->st, h->stream, i > 0 ? 1 : 0);
             h->ops->passB(h->pd, h->st, h->stream);
-            cudaEventRecord(ev[3 * i + 2], h->stream);
-            h->ops->finish(h->pd, h->st, h->stream);
         }
-        cudaEventRecord(ev[3 * size_t(iters)], h->stream);
-        const cudaError_t ce = cudaEventSynchronize(ev[3 * size_t(iters)]);
-        if (ce != cudaSuccess) rc = cuda_fail(ce, "profile iterations");
-    }
-    double ta = 0.0, tb = 0.0, tf = 0.0;
-    if (rc == FW_OK) {
-        for (int i = 0; i < iters; ++i) {
-            float a = 0.f, b = 0.f, f = 0.f;
-            cudaEventElapsedTime(&a, ev[3 * i], ev[3 * i + 1]);
-            cudaEventElapsedTime(&b, ev[3 * i + 1], ev[3 * i + 2]);
-            cudaEventElapsedTime(&f, ev[3 * i + 2], ev[3 * i + 3]);
-            ta += a;
-            tb += b;
-            tf += f;
-        }
-    }
-    for (auto& e : ev)
-        if (e) cudaEventDestroy(e);
-    if (rc != FW_OK) return rc;
-    if (ms_a) *ms_a = ta / iters;
-    if (ms_b) *ms_b = tb / iters;
-    if (ms_f) *ms_f = tf / iters;
+        h->ops->finish(h->pd, h->st, h->stream);
+    }, e0, e1, &t_ab));
+    FW_TRY(read_state(h));
+    if (h->h_state->done)
+        return invalid("the stop rule held while profiling: reset and profile fewer iterations");
+    // 2. one more iteration without its finish: its totals wait in bank cur,
+    //    the state a fused pass A starts from
+    h->ops->passA(h->pd, h->st, h->stream, 0);
+    h->ops->passB(h->pd, h->st, h->stream);
+    FW_TRY(launch_check("profile kernels"));
+    Temps t(h->stream);
+    Snapshot s;
+    const size_t blk = h->ops->elem() * size_t(h->lay.npad) * size_t(h->lay.K);
+    FW_TRY(t.get(&s.U, blk));
+    FW_TRY(t.get(&s.LU, blk));
+    FW_TRY(t.get(&s.LS, blk));
+    FW_TRY(t.get(&s.ch, size_t(h->lay.n)));
+    FW_TRY(t.get(&s.c4, size_t(h->lay.n) / 2 + 1));
+    FW_TRY(t.get(&s.acc, 8 * size_t(kAccTotal)));
+    FW_TRY(t.get(&s.st, sizeof(ProbState)));
+    FW_TRY(copy_problem_state(h, s, true));
+    // 3. m launches of pass B back to back (each recomputes the same L S)
+    FW_TRY(time_enqueued(h, graph, [&] {
+        for (int i = 0; i < m; ++i) h->ops->passB(h->pd, h->st, h->stream);
+    }, e0, e1, &t_b));
+    FW_TRY(copy_problem_state(h, s, false));
+    // 4. m launches of the fused pass A back to back (each takes the same
+    //    decision from bank cur and applies it once more)
+    FW_TRY(time_enqueued(h, graph, [&] {
+        for (int i = 0; i < m; ++i) h->ops->passA(h->pd, h->st, h->stream, 1);
+    }, e0, e1, &t_a));
+    FW_TRY(copy_problem_state(h, s, false));
+    // 5. the finishing kernel of that iteration, which also leaves the
+    //    handle in a consistent state (iters + 1 iterations done)
+    FW_TRY(time_enqueued(h, false, [&] { h->ops->finish(h->pd, h->st, h->stream); }, e0, e1,
+                         &t_f));
+    if (ms_a) *ms_a = double(t_a) / m;
+    if (ms_b) *ms_b = double(t_b) / m;
+    if (ms_f) *ms_f = double(t_f);
+    if (ms_iter) *ms_iter = double(t_ab) / m;
+    if (in_graph) *in_graph = graph ? 1 : 0;
+    h->launches += 2 * m + 1 + 2 + 2 * m + 1;
+    FW_TRY(read_state(h));
     return flush(h);
 }
 

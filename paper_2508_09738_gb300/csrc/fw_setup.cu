@@ -466,6 +466,10 @@ fw_status restart_problem(Ops* ops, const ProbDesc& pd, ProbState* st, bool from
 
 fw_status check_graph_args(const HostGraph& g) {
     if (g.n < 1 || g.n >= (int64_t(1) << 31) - 1) return invalid("n must be in [1, 2^31-1)");
+    if (g.K < 2 || g.K > 32) {
+        set_error("K must be in [2, 32]");
+        return FW_ERR_UNSUPPORTED;
+    }
     if (!g.rp || !g.labels) return invalid("row_ptr and labels must not be NULL");
     if (g.rp[0] != 0) {
         set_error("row_ptr[0] must be 0");

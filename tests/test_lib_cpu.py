@@ -90,6 +90,22 @@ def test_invalid_arguments_rejected_before_device_use(libpath):
     assert e.value.status == Bd.FW_ERR_INVALID_ARG
 
 
+def test_large_input_size_checks_before_upload(libpath):
+    """Inputs of at least 2^20 rows are uploaded before the host's planning
+    pass; K outside [2, 32] is still rejected before any device call."""
+    from paper_2508_09738_gb300 import binding as Bd
+    import numpy as np
+    n = 1 << 20
+    rp = np.arange(n + 1, dtype=np.int32)          # never read beyond rp[0] and rp[n]
+    col = np.zeros(n, np.int32)
+    w = np.ones(n)
+    lab = np.full(n, -1, np.int32)
+    for K in (1, 33):
+        with pytest.raises(Bd.FwError) as e:
+            Bd.fw_seg_create(n, rp, col, w, K, lab)
+        assert e.value.status == Bd.FW_ERR_UNSUPPORTED
+
+
 def test_noalloc_energy_host_checks(libpath):
     """fw_energy_noalloc rejects sizes above its static scratch and bad
     arguments on the host, before any device pointer is touched."""
