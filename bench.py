@@ -1,10 +1,13 @@
 #!/usr/bin/env python
 """Benchmark of the GPU Greedy Frank-Wolfe path: FW iterations per second.
 
-One step = one full solve (reset to U_0, then `iters` GFW iterations) of the
-200,000-node stochastic-block-model workload (K = 10, FP32 weights and iterate,
-eps = 50, omega_0 = 1000), with the graph resident in HBM.  Under torchrun each
-rank solves its own replica (weak scaling, no data-path collective).
+Default workload: the 2048 x 2048 noisy Voronoi image (n = 4,194,304 pixels,
+8-neighbour graph, 33,529,860 stored entries, K = 4, eps = 50, omega_0 = 1e5,
+200 GFW iterations per solve), the largest single-GPU configuration.  One step
+= one full solve (reset to U_0, then the iterations) with the graph resident
+in HBM.  The line's headline numbers are for FP32 weights; the same run times
+BF16 weights as a second record.  Under torchrun each rank solves its own
+replica (weak scaling, no data-path collective).
 
 Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle on
 the host cores on the same workload instead.
@@ -15,6 +18,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -31,6 +35,7 @@ from paper_2508_09738_gb300 import workloads as W  # noqa: E402
 
 METRIC = "FW iters/s"
 L2_FLUSH_BYTES = 256 << 20
+GOLDEN = os.path.join(ROOT, "tests", "golden")
 
 
 def parse():
@@ -39,21 +44,24 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="sbm200k")
+    p.add_argument("--workload", default="voronoi2048")
     p.add_argument("--iters", type=int, default=0, help="iterations per solve (default: config)")
     p.add_argument("--iters-per-launch", type=int, default=0)
     p.add_argument("--lanes", type=int, default=0)
-    p.add_argument("--weights", default="")
+    p.add_argument("--weights", default="", help="one weight dtype instead of the config's arms")
     p.add_argument("--profile-iters", type=int, default=100)
-    p.add_argument("--cpu-iters", type=int, default=0, help="oracle iterations in the CPU sample")
+    p.add_argument("--cpu-seconds", type=float, default=15.0,
+                   help="target length of each CPU-oracle sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-trajectory", action="store_true")
     return p.parse_args()
 
 
 # ------------------------------------------------------------------ clocks --
 class ClockSampler:
-    """nvidia-smi samples (200 ms) during the timed region."""
+    """nvidia-smi samples (200 ms) during the timed regions: start() / stop()
+    around each timed region, summary() over all of them."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -62,6 +70,8 @@ class ClockSampler:
         self.index = index
         self.proc = None
         self.path = None
+        self.rows = []
+        self.failed = False
 
     def start(self):
         try:
@@ -73,22 +83,28 @@ class ClockSampler:
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            self.failed = True
 
-    def stop(self) -> dict:
+    def stop(self):
         if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+            return
         time.sleep(0.25)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        rows = []
         for line in open(self.path):
             f = [x.strip() for x in line.split(",")]
             if len(f) >= 9:
-                rows.append(f)
+                self.rows.append(f)
         os.unlink(self.path)
+        self.proc = None
+
+    def summary(self) -> dict:
+        if self.failed and not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = self.rows
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
         smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
@@ -100,7 +116,11 @@ class ClockSampler:
 
 # ---------------------------------------------------------- byte counting --
 def bytes_per_unit(n, nnz, K, wbytes, tbytes=4):
-    """Algorithmic bytes of one FW iteration and of each pass."""
+    """Algorithmic bytes of one FW iteration (the method's minimum: U and L U
+    read and written, the CSR once, row_ptr, choice and fidelity bytes) and of
+    each pass of the two-pass design (pass A: U, L U, L S in, U, L U out;
+    pass B: U in for the moved rows, L S out, the CSR, row_ptr, the row's own
+    choice and the gathered neighbour classes)."""
     row_pass = 5 * tbytes * n * K + 3 * n                 # U, LU, LS in; U, LU out; choice, fid
     csr_pass = (2 * tbytes * n * K + (4 + wbytes) * nnz   # U in, LS out; col + weights
                 + 4 * (n + 1) + 2 * n)                    # row_ptr; choice of the row + gathers
@@ -146,48 +166,158 @@ def ncu_traffic(kernel: str, workload: str):
 
 
 # ---------------------------------------------------------------- oracle --
-def cpu_oracle_rate(g, c, iters):
-    """Oracle iterations/s on a bounded sample: `iters` GFW iterations from U_0."""
+def cpu_model() -> str:
+    """The host CPU's model name (/proc/cpuinfo, else lscpu)."""
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.processor() or platform.machine()
+
+
+def _oracle_problem(g, c, weights):
     import oracle as O
-    P = O.make_problem(g, c["eps"], c["omega0"], c["weights"])
+    return O.make_problem(g, c["eps"], c["omega0"], weights)
+
+
+def oracle_sample_iters(g, c, weights, seconds):
+    """Iterations of an oracle sample that take about `seconds` on one core
+    (from the time of one GFW iteration at U_0)."""
+    import oracle as O
+    P = _oracle_problem(g, c, weights)
+    t = time.perf_counter()
+    O.gfw_iteration(P.Uhat, P)
+    dt = time.perf_counter() - t
+    return int(min(500, max(2, round(seconds / max(dt, 1e-6))))), dt
+
+
+def cpu_oracle_rate(g, c, weights, iters):
+    """Oracle iterations/s on one thread: `iters` GFW iterations from U_0."""
+    import oracle as O
+    P = _oracle_problem(g, c, weights)
     t = time.perf_counter()
     U, info = O.gfw_solve(P, max_iters=iters)
     dt = time.perf_counter() - t
     return info["iters"] / dt, dt, info["iters"]
 
 
+def _oracle_replica(path, c, weights, iters, steps, barrier, q):
+    """One replica process of the oracle: load the graph, build the problem
+    (not timed), then per step wait for the other replicas and time `iters`
+    GFW iterations from U_0."""
+    import oracle as O
+    d = np.load(path)
+    g = W.Graph(int(d["n"]), d["row_ptr"], d["col"], d["w"], int(d["K"]), d["labels"],
+                d["labels"])
+    P = O.make_problem(g, c["eps"], c["omega0"], weights)
+    for _ in range(steps):
+        barrier.wait()
+        t = time.perf_counter()
+        _, info = O.gfw_solve(P, max_iters=iters)
+        q.put((info["iters"], time.perf_counter() - t))
+
+
+def cpu_oracle_replicas(g, c, weights, iters, procs, steps=1):
+    """The oracle as it stands on `procs` host cores: `procs` spawned
+    processes, each solving its own copy of the problem (the oracle itself
+    is single-threaded).  Returns per step (iterations of all replicas, the
+    slowest replica's seconds)."""
+    import multiprocessing as mp
+    env = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS",
+                                          "MKL_NUM_THREADS")}
+    for k in env:
+        os.environ[k] = "1"
+    fd, path = tempfile.mkstemp(suffix=".npz")
+    os.close(fd)
+    try:
+        np.savez(path, n=g.n, K=g.K, row_ptr=g.row_ptr, col=g.col, w=g.w, labels=g.labels)
+        ctx = mp.get_context("spawn")
+        barrier = ctx.Barrier(procs)
+        q = ctx.Queue()
+        ps = [ctx.Process(target=_oracle_replica, args=(path, c, weights, iters, steps, barrier, q))
+              for _ in range(procs)]
+        for p_ in ps:
+            p_.start()
+        out = []
+        for _ in range(steps):
+            res = [q.get(timeout=3600) for _ in range(procs)]
+            out.append((sum(r[0] for r in res), max(r[1] for r in res)))
+        for p_ in ps:
+            p_.join(timeout=600)
+        return out
+    finally:
+        os.unlink(path)
+        for k, v in env.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+
+def cpu_baseline(g, c, weights, seconds):
+    """The oracle timed on one thread and on every host core (replicas)."""
+    iters, t1 = oracle_sample_iters(g, c, weights, seconds)
+    v1, dt1, it1 = cpu_oracle_rate(g, c, weights, iters)
+    T = os.cpu_count() or 1
+    (tot, dtT), = cpu_oracle_replicas(g, c, weights, iters, T)
+    vT = tot / dtT
+    return {"value": vT, "unit": "iter/s", "cores": T, "kind": "oracle",
+            "cpu_model": cpu_model(),
+            "sample": f"{T} processes, each running the first {iters} GFW iterations from U_0 "
+                      f"of its own copy of this workload (numpy/scipy FP64, "
+                      f"{weights}-rounded weights), {dtT:.1f} s; one process alone: "
+                      f"{it1} iterations in {dt1:.1f} s",
+            "single_thread": {"value": v1, "unit": "iter/s", "cores": 1, "seconds": dt1,
+                              "iterations": it1}}
+
+
 def run_reference(args, c, rank):
+    """The reference arm: the FP64 oracle as it stands on every host core (one
+    replica process per core), each step a bounded sample of the workload."""
     if rank != 0:
         return
     g = W.make_config_graph(args.workload)
-    iters = args.cpu_iters or max(2, int(20 * 200_000 / g.n))
-    for _ in range(args.warmup):
-        cpu_oracle_rate(g, c, iters)
-    total, done = 0.0, 0
-    for _ in range(args.steps):
-        _, dt, it = cpu_oracle_rate(g, c, iters)
-        total += dt
-        done += it
+    weights = args.weights or c["weights"]
+    per_step = max(1.0, 120.0 / max(1, args.steps + args.warmup))
+    iters, _ = oracle_sample_iters(g, c, weights, per_step)
+    T = os.cpu_count() or 1
+    res = cpu_oracle_replicas(g, c, weights, iters, T, steps=args.warmup + args.steps)
+    timed = res[args.warmup:]
+    total = sum(dt for _, dt in timed)
+    done = sum(it for it, _ in timed)
     v = done / total
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "iter/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000 * total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": config_dict(args, c, g, args.iters or c["iters"]),
-        "cpu_baseline": {"value": v, "unit": "iter/s", "cores": 1, "kind": "oracle",
-                         "sample": f"each step: the first {iters} GFW iterations from U_0 of "
-                                   f"that solve (numpy/scipy FP64, one thread)"},
+        "config": config_dict(args, c, g, args.iters or c["iters"], weights),
+        "cpu_baseline": {"value": v, "unit": "iter/s", "cores": T, "kind": "oracle",
+                         "cpu_model": cpu_model(),
+                         "sample": f"each step: {T} processes, each running the first {iters} GFW "
+                                   f"iterations from U_0 of its own copy of the workload "
+                                   f"(numpy/scipy FP64, {weights}-rounded weights)"},
         "e2e": {"value": v, "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-def config_dict(args, c, g, iters):
+def config_dict(args, c, g, iters, weights):
+    wb = {"f32": 4, "bf16": 2, "f64": 8}[weights]
     return {"workload": args.workload, "n": g.n, "nnz": g.nnz, "K": g.K,
-            "iters_per_solve": iters, "weights": args.weights or c["weights"],
+            "iters_per_solve": iters, "weights": weights,
             "eps": c["eps"], "omega0": c["omega0"],
-            "l2": "256 MiB buffer written between timed steps",
+            "l2": "256 MiB buffer written between timed steps; CSR %.0f MB" %
+                  ((4 + wb) * g.nnz / 1e6),
             "parallelism": f"replicas x{args.gpus}"}
 
 
@@ -256,7 +386,8 @@ def run_batched(args, rank, world, local):
     clocks = ClockSampler(local)
     clocks.start()
     t_b, stats = timed(batched_step, args.steps)
-    clk = clocks.stop()
+    clocks.stop()
+    clk = clocks.summary()
     total_iters = sum(s_.iters for s_ in stats)
     # the plain one-problem-at-a-time path on the same problems, resident on the device
     segs = [B.Segmenter(g, max_iters=iters, weight_dtype=weights, iters_per_launch=iters,
@@ -457,7 +588,8 @@ def run_oneshot(args, rank, world, local):
     torch.cuda.synchronize()
     clocks.start()
     kms = [seg.oneshot(with_labels=False)[1] for _ in range(args.steps)]
-    clk = clocks.stop()
+    clocks.stop()
+    clk = clocks.summary()
     value, t_s = whole_job_rate(args.steps, sum(kms) / 1000.0, world, "cuda")
     lab, _ = seg.oneshot()
     # the GFW path: reset + solve stops after its single step (alpha = 1)
@@ -540,22 +672,184 @@ def cpu_oracle_oneshot(g, c):
     return 1.0 / dt, dt, s
 
 
-def main():
-    args = parse()
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if args.workload == "batched256":
-        return run_batched(args, rank, world, local)
-    if args.workload == "serving":
-        return run_serving(args, rank, world, local)
-    if args.workload == "oneshot":
-        return run_oneshot(args, rank, world, local)
-    c = W.CONFIGS[args.workload]
-    if args.impl == "reference":
-        run_reference(args, c, rank)
-        return
+# ---------------------------------------------------------- stored oracle --
+def golden(workload, iters, weights):
+    """The stored FP64 oracle run of this workload, if there is one
+    (tests/golden/make_oracle_golden.py)."""
+    p = os.path.join(GOLDEN, f"{workload}_oracle{iters}_{weights}.npz")
+    return np.load(p) if os.path.exists(p) else None
 
+
+def rel(a, b):
+    return abs(a - b) / max(abs(b), 1e-300)
+
+
+def trajectory(seg, iters):
+    """(g_k, q_k, alpha_k, E_{k+1}) of iterations k = 0.. of a stepwise run from
+    U_0; stepwise runs are bitwise the solve's trajectory."""
+    seg.reset()
+    out = []
+    for _ in range(iters):
+        st = seg.step(1)
+        out.append((st.gap, st.q, st.alpha, st.objective))
+        if st.status != 2:   # FW_PENDING: not stopped
+            break
+    return np.array(out)
+
+
+def compare_golden(gold, labels, E_gpu, traj, truth):
+    """Agreement of a GPU solve with the stored oracle run: labels, the final
+    objective, accuracy against the generator's truth, and the per-iteration
+    gap, curvature, step and objective."""
+    ref = gold["labels"].astype(np.int32)
+    off = ref != 0
+    d = {"label_agreement": float(np.mean(labels == ref)),
+         "label_agreement_off_class0": {
+             "value": float(np.mean(labels[off] == ref[off])) if off.any() else None,
+             "rows": int(off.sum())},
+         "objective_rel_err": rel(E_gpu, float(gold["energy"])),
+         "accuracy_vs_truth": {"gpu": float(np.mean(labels == truth)),
+                               "oracle": float(gold["accuracy"])}}
+    if traj is not None and "q" in gold:
+        m = min(len(traj), len(gold["gap"]) - 1)
+        t = {}
+        for name, col, ref_arr in (("gap", 0, gold["gap"][:m]), ("q", 1, gold["q"][:m]),
+                                   ("alpha", 2, gold["alpha"][:m]),
+                                   ("objective", 3, gold["E"][1:m + 1])):
+            e = np.abs(traj[:m, col] - ref_arr) / np.maximum(np.abs(ref_arr), 1e-300)
+            t[name] = {"max_rel": float(e.max()), "median_rel": float(np.median(e)),
+                       "at_iter": int(e.argmax())}
+        t["iterations"] = m
+        d["trajectory_vs_oracle"] = t
+    return d
+
+
+def roofline_of(prof, g, weights, workload, peaks):
+    wb = {"f32": 4, "bf16": 2, "f64": 8}[weights]
+    tb = 8 if weights == "f64" else 4
+    by = bytes_per_unit(g.n, g.nnz, g.K, wb, tb)
+    dom = "csr_pass" if prof["pass_b"] >= prof["pass_a"] else "row_pass"
+    dom_ms = prof["pass_b"] if dom == "csr_pass" else prof["pass_a"]
+    kernel = {"csr_pass": "k_passB", "row_pass": "k_passA"}[dom]
+    achieved = by[dom] / (dom_ms / 1000.0) / 1e9
+    key = workload if weights == "f32" else f"{workload}_{weights}"
+    return {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": ncu_traffic(kernel, key),
+            "kernel": kernel, "peak_source": peaks["source"],
+            "algorithmic_bytes_per_launch": by[dom],
+            "timing": "CUDA events on the solver's stream around a captured graph of "
+                      "back-to-back launches of the kernel" if prof["in_graph"] else
+                      "CUDA events around back-to-back direct launches of the kernel",
+            "kernel_ms": {"k_passA": prof["pass_a"], "k_passB": prof["pass_b"],
+                          "k_finish": prof["finish"]}}, by
+
+
+def time_arm(args, B, torch, g, c, weights, iters, stream, flush, clocks, world, rank):
+    """Warm-up and timed solves of one weight dtype, then its in-graph kernel
+    times and (rank 0) its stepwise trajectory."""
+    import torch.distributed as dist
+    ipl = args.iters_per_launch or 32     # the library default
+    opts = dict(eps=c["eps"], omega0=c["omega0"], weight_dtype=weights, max_iters=iters,
+                iters_per_launch=ipl, lanes_per_row=args.lanes, cuda_stream=stream.cuda_stream)
+    seg = B.Segmenter(g, **opts)
+    for _ in range(args.warmup):
+        flush.zero_()
+        seg.reset()
+        seg.solve()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches = 0
+    st = None
+    for s in range(args.steps):
+        flush.zero_()
+        ev[s][0].record(stream)
+        seg.reset()
+        st = seg.solve()
+        ev[s][1].record(stream)
+        launches += st.launches + 4     # reset: reinit, L U_hat, objective, state
+    torch.cuda.synchronize()
+    clocks.stop()
+    t_ms = sum(a.elapsed_time(b) for a, b in ev)
+    value, t_s = whole_job_rate(args.steps * st.iters, t_ms / 1000.0, world, "cuda")
+    labels = seg.labels()
+    E = seg.objective()
+    seg.reset()
+    prof = seg.profile(min(args.profile_iters, iters))
+    traj = None if (args.no_trajectory or rank != 0) else trajectory(seg, iters)
+    seg.close()
+    return dict(value=value, t_s=t_s, iters=st.iters, launches=launches, labels=labels, E=E,
+                prof=prof, traj=traj, opts=opts)
+
+
+def arm_record(args, arm, g, c, weights, iters, world, peaks):
+    """The JSON fields of one timed weight dtype."""
+    roof, by = roofline_of(arm["prof"], g, weights, args.workload, peaks)
+    ms_step = 1000.0 * arm["t_s"] / args.steps
+    rec = {"value": arm["value"], "unit": "iter/s", "weights": weights,
+           "ms_per_step": ms_step, "solves_per_s": world * args.steps / arm["t_s"],
+           "effective_gbs": by["iteration"] * arm["value"] / world / 1e9,
+           "gpu_launches": arm["launches"], "roofline": roof,
+           "per_iteration_ms": {
+               "timed_step": ms_step / max(1, arm["iters"]),
+               "fused_graph": arm["prof"]["per_iter"],
+               "passes": arm["prof"]["pass_a"] + arm["prof"]["pass_b"]
+               + arm["prof"]["finish"] / arm["opts"]["iters_per_launch"],
+               "note": "timed_step: the timed solves per iteration, reset (U_0, L U_0, E_0) "
+                       "included; fused_graph: a graph of the solve's fused iterations; "
+                       "passes: graphs of back-to-back pass A and pass B launches plus one "
+                       "finish per graph launch of the solve"}}
+    gold = golden(args.workload, iters, weights)
+    if gold is not None and int(gold["nnz"]) == g.nnz:
+        rec.update(compare_golden(gold, arm["labels"], arm["E"], arm["traj"], g.truth))
+    else:
+        rec["accuracy_vs_truth"] = {"gpu": float(np.mean(arm["labels"] == g.truth))}
+    return rec
+
+
+def e2e_rate(args, B, torch, g, opts, world):
+    """The same metric through the C ABI from pinned host buffers: create
+    (upload, validation, assembly, L U_0), solve, labels to the host, destroy."""
+    import torch.distributed as dist
+
+    def pinned(a):
+        t = torch.empty(a.shape, dtype=getattr(torch, str(a.dtype)), pin_memory=True)
+        t.numpy()[...] = a
+        return t
+    rp, col, w, lab = (pinned(g.row_ptr), pinned(g.col), pinned(g.w), pinned(g.labels))
+    out = torch.empty(g.n, dtype=torch.int32, pin_memory=True)
+    o = B.fw_seg_default_opts(**opts)
+    steps_e2e = max(1, min(args.steps, 3))
+    h = B.fw_seg_create(g.n, rp.numpy(), col.numpy(), w.numpy(), g.K, lab.numpy(), o)
+    B.fw_seg_solve(h)
+    B.fw_seg_destroy(h)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    it_e2e = 0
+    for _ in range(steps_e2e):
+        h = B.fw_seg_create(g.n, rp.numpy(), col.numpy(), w.numpy(), g.K, lab.numpy(), o)
+        st = B.fw_seg_solve(h)
+        B.fw_seg_labels(h, out.numpy())
+        B.fw_seg_destroy(h)
+        it_e2e += st.iters
+    dt = time.perf_counter() - t0
+    rate, _ = whole_job_rate(it_e2e, dt, world, "cuda")
+    return {"value": rate, "unit": "iter/s",
+            "h2d_bytes_per_step": int(4 * (g.n + 1) + 12 * g.nnz + 4 * g.n),
+            "d2h_bytes_per_step": int(4 * g.n), "steps": steps_e2e,
+            "includes": "create (H2D, validation, Laplacian assembly, L U_0), solve, labels "
+                        "D2H, destroy"}
+
+
+def run_single(args, rank, world, local):
+    """One problem per GPU (replicas under torchrun): every weight dtype of
+    the workload's arms, the first one the line's headline."""
     import torch
     import torch.distributed as dist
     torch.cuda.set_device(local)
@@ -568,129 +862,61 @@ def main():
         dist.barrier()
     from paper_2508_09738_gb300 import binding as B
 
-    weights = args.weights or c["weights"]
+    c = W.CONFIGS[args.workload]
+    arms = [args.weights] if args.weights else list(c.get("arms", (c["weights"],)))
     iters = args.iters or c["iters"]
     g = W.make_config_graph(args.workload)
     stream = torch.cuda.Stream()          # one stream for flush, events and solver
     torch.cuda.set_stream(stream)
-    ipl = args.iters_per_launch or 32     # the library default: short graph capture at create
-    opts = dict(eps=c["eps"], omega0=c["omega0"], weight_dtype=weights, max_iters=iters,
-                iters_per_launch=ipl, lanes_per_row=args.lanes, cuda_stream=stream.cuda_stream)
-    seg = B.Segmenter(g, **opts)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
-
-    for _ in range(args.warmup):
-        flush.zero_()
-        seg.reset()
-        seg.solve()
-    torch.cuda.synchronize()
-
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
     clocks = ClockSampler(local)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    launches = 0
-    stats = None
-    for s in range(args.steps):
-        flush.zero_()
-        ev[s][0].record(stream)
-        seg.reset()
-        stats = seg.solve()
-        ev[s][1].record(stream)
-        launches += stats.launches + 4     # reset: reinit, spmm, spmm, objective
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    t_ms = sum(a.elapsed_time(b) for a, b in ev)
-    value, t_s = whole_job_rate(args.steps * stats.iters, t_ms / 1000.0, world, "cuda")
-    t_ms = 1000.0 * t_s
-    if world > 1:
-        dist.barrier()
-    labels = seg.labels()
-    solves = world * args.steps / t_s
-
-    # per-pass device times (CUDA events on the solver's stream) -> roofline
-    seg.reset()
-    ms_a, ms_b, ms_f = seg.profile(min(args.profile_iters, iters))
-    wb = {"f32": 4, "bf16": 2, "f64": 8}[weights]
-    tb = 8 if weights == "f64" else 4
-    by = bytes_per_unit(g.n, g.nnz, g.K, wb, tb)
-    dom = "csr_pass" if ms_b >= ms_a else "row_pass"
-    dom_ms = max(ms_a, ms_b)
     peaks = load_peaks()
-    achieved = by[dom] / (dom_ms / 1000.0) / 1e9
-    kernel_name = {"csr_pass": "k_passB", "row_pass": "k_passA"}[dom]
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"],
-                "traffic": ncu_traffic(kernel_name, args.workload),
-                "kernel": kernel_name, "peak_source": peaks["source"],
-                "algorithmic_bytes_per_launch": by[dom],
-                "kernel_ms": {"k_passA": ms_a, "k_passB": ms_b, "k_finish": ms_f}}
-    seg.close()
-
-    # end to end through the C ABI from pinned host buffers
-    e2e = None
-    if not args.no_e2e:
-        def pinned(a):
-            t = torch.empty(a.shape, dtype=getattr(torch, str(a.dtype)), pin_memory=True)
-            t.numpy()[...] = a
-            return t
-        rp, col, w, lab = (pinned(g.row_ptr), pinned(g.col), pinned(g.w), pinned(g.labels))
-        out = torch.empty(g.n, dtype=torch.int32, pin_memory=True)
-        o = B.fw_seg_default_opts(**opts)
-        steps_e2e = max(1, min(args.steps, 3))
-        h = B.fw_seg_create(g.n, rp.numpy(), col.numpy(), w.numpy(), g.K, lab.numpy(), o)
-        B.fw_seg_solve(h)
-        B.fw_seg_destroy(h)
-        torch.cuda.synchronize()
-        if world > 1:
-            dist.barrier()
-        t0 = time.perf_counter()
-        it_e2e = 0
-        for _ in range(steps_e2e):
-            h = B.fw_seg_create(g.n, rp.numpy(), col.numpy(), w.numpy(), g.K, lab.numpy(), o)
-            st = B.fw_seg_solve(h)
-            B.fw_seg_labels(h, out.numpy())
-            B.fw_seg_destroy(h)
-            it_e2e += st.iters
-        dt = time.perf_counter() - t0
-        e2e_rate, dt = whole_job_rate(it_e2e, dt, world, "cuda")
-        e2e = {"value": e2e_rate, "unit": "iter/s",
-               "h2d_bytes_per_step": int(4 * (g.n + 1) + 12 * g.nnz + 4 * g.n),
-               "d2h_bytes_per_step": int(4 * g.n),
-               "steps": steps_e2e, "includes": "create (H2D, validation, Laplacian assembly, "
-                                                "L U_0), solve, labels D2H, destroy"}
-
+    res = {w: time_arm(args, B, torch, g, c, w, iters, stream, flush, clocks, world, rank)
+           for w in arms}
+    clk = clocks.summary()
+    e2e = None if args.no_e2e else e2e_rate(args, B, torch, g, res[arms[0]]["opts"], world)
+    if world > 1:
+        dist.barrier()
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return
-
+    recs = {w: arm_record(args, res[w], g, c, w, iters, world, peaks) for w in arms}
+    head = recs[arms[0]]
     line = {
-        "metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if weights == "f64" else "f32", "data": "synthetic",
-        "config": config_dict(args, c, g, iters),
-        "solves_per_s": solves,
-        "effective_gbs": by["iteration"] * value / world / 1e9,
-        "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
+        "metric": METRIC, "value": head.pop("value"), "unit": head.pop("unit"),
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": head.pop("ms_per_step"), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if arms[0] == "f64" else "f32",
+        "data": "synthetic", "config": config_dict(args, c, g, iters, arms[0]),
+        "clocks": clk, "e2e": e2e, "gpu_launches": head.pop("gpu_launches"),
+        "roofline": head.pop("roofline"),
     }
-    gold = os.path.join(ROOT, "tests", "golden", f"{args.workload}_oracle{iters}.npz")
-    if os.path.exists(gold) and weights == c["weights"]:
-        ref = np.load(gold)
-        line["label_agreement"] = float(np.mean(labels == ref["labels"]))
+    head.pop("weights")
+    line.update(head)
+    for w in arms[1:]:
+        line[w] = recs[w]
     if not args.no_cpu_baseline and world == 1:
-        ci = args.cpu_iters or max(2, int(40 * 200_000 / g.n))
-        v, dt, it = cpu_oracle_rate(g, c, ci)
-        line["cpu_baseline"] = {"value": v, "unit": "iter/s", "cores": 1, "kind": "oracle",
-                                "sample": f"{it} GFW iterations from U_0 on the same graph "
-                                          f"(numpy/scipy FP64, one thread), {dt:.1f} s"}
+        line["cpu_baseline"] = cpu_baseline(g, c, arms[0], args.cpu_seconds)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.workload == "batched256":
+        return run_batched(args, rank, world, local)
+    if args.workload == "serving":
+        return run_serving(args, rank, world, local)
+    if args.workload == "oneshot":
+        return run_oneshot(args, rank, world, local)
+    if args.impl == "reference":
+        return run_reference(args, W.CONFIGS[args.workload], rank)
+    return run_single(args, rank, world, local)
 
 
 if __name__ == "__main__":

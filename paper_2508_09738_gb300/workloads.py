@@ -319,8 +319,9 @@ CONFIGS = {
     "sbm200k": dict(gen="sbm", seed=SEED0 + 1, n=200_000, K=10, label_frac=0.01,
                     eps=50.0, omega0=1000.0, iters=500, weights="f32"),
     # 2048 x 2048 noisy Voronoi image, K = 4, 8-neighbour graph
+    # (measured with FP32 weights and, in the same run, with BF16 weights)
     "voronoi2048": dict(gen="voronoi", seed=SEED0 + 2, side=2048, K=4, label_frac=0.005,
-                        eps=50.0, omega0=1e5, iters=200, weights="f32"),
+                        eps=50.0, omega0=1e5, iters=200, weights="f32", arms=("f32", "bf16")),
     "voronoi2048_oneshot": dict(gen="voronoi", seed=SEED0 + 2, side=2048, K=4,
                                 label_frac=0.005, eps=0.1, omega0=1e5, iters=10,
                                 weights="f32"),
