@@ -361,7 +361,6 @@ def run_batched(args, rank, world, local):
     t0 = time.time()
     bt = B.Batch(gs, opts, weight_dtype=weights, cuda_stream=stream.cuda_stream, tune_cache=cache)
     create_s = time.time() - t0
-    info = bt.info().as_dict()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
     def timed(fn, steps):
@@ -383,6 +382,7 @@ def run_batched(args, rank, world, local):
     for _ in range(args.warmup):
         batched_step()
     torch.cuda.synchronize()
+    info = bt.info().as_dict()         # after solves: the launch as it ran
     clocks = ClockSampler(local)
     clocks.start()
     t_b, stats = timed(batched_step, args.steps)
@@ -391,7 +391,8 @@ def run_batched(args, rank, world, local):
     total_iters = sum(s_.iters for s_ in stats)
     # the plain one-problem-at-a-time path on the same problems, resident on the device
     segs = [B.Segmenter(g, max_iters=iters, weight_dtype=weights, iters_per_launch=iters,
-                        cuda_stream=stream.cuda_stream) for g in gs]
+                        lanes_per_row=info["lanes_per_row"], cuda_stream=stream.cuda_stream)
+            for g in gs]
 
     def sequential_step():
         it = 0
@@ -406,6 +407,18 @@ def run_batched(args, rank, world, local):
     same = all(np.array_equal(bt.labels(p), segs[p].labels()) for p in range(P))
     for sg in segs:
         sg.close()
+    # the FP64 oracle on the same rounded weights, for the smallest problems
+    sample = []
+    if not args.no_cpu_baseline:
+        import oracle as O
+        for p in sorted(range(P), key=lambda q: gs[q].n)[:4]:
+            Pp = O.make_problem(gs[p], 50.0, 1000.0, weights)
+            Uo, _ = O.gfw_solve(Pp, max_iters=iters)
+            Eo = O.energy(Uo, Pp)
+            sample.append({"problem": p, "n": gs[p].n, "K": gs[p].K,
+                           "label_agreement": float(np.mean(bt.labels(p) ==
+                                                            O.labels_from_U(Uo))),
+                           "objective_rel_err": rel(O.energy(bt.U(p), Pp), Eo)})
     wb = {"f32": 4, "bf16": 2, "f64": 8}[weights]
     byt = sum(bytes_per_unit(g.n, g.nnz, g.K, wb)["iteration"] * st.iters
               for g, st in zip(gs, stats))
@@ -426,6 +439,7 @@ def run_batched(args, rank, world, local):
                              "ms_per_step": 1000 * t_s / steps_seq},
         "speedup_vs_sequential": (P * args.steps / t_b) / (P * steps_seq / t_s),
         "labels_equal_to_single": same, "batch_info": info, "clocks": clk,
+        "oracle_sample": sample,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                      "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
                      "kernel": "k_persistent", "peak_source": peaks["source"],
@@ -486,7 +500,8 @@ def run_serving(args, rank, world, local):
             lam = mult * cap
             arr = np.cumsum(rng.exponential(1.0 / lam, size=R))
             pick = rng.integers(0, len(pool), size=R)
-            # served: submit on schedule, poll for completions
+            # served: submit on schedule; between arrivals, sleep in the server
+            # until a request finishes (or the next arrival is due)
             lat, t_start = [], time.perf_counter()
             pending = {}
             i = 0
@@ -497,15 +512,15 @@ def run_serving(args, rank, world, local):
                     g, o = pool[pick[i]]
                     pending[srv.submit(g, **o, **common)] = (i, arr[i])
                     i += 1
-                for tk in list(pending):
-                    idx, ta = pending[tk]
+                wait_ms = int((arr[i] - now) * 1000.0) if i < R else 1000
+                rc, tk = srv.wait_any(max(0, wait_ms))
+                if rc == B.FW_OK and tk in pending:
+                    done_t = time.perf_counter() - t_start
+                    idx, ta = pending.pop(tk)
                     g, _ = pool[pick[idx]]
-                    rc, lab, st = srv.poll(tk, g.n)
-                    if rc != B.FW_PENDING:
-                        lat.append(time.perf_counter() - t_start - ta)
-                        equal &= bool(np.array_equal(lab, alone[pick[idx]][0]))
-                        del pending[tk]
-                time.sleep(0.0005)
+                    rc2, lab, st = srv.poll(tk, g.n)
+                    lat.append(done_t - ta)
+                    equal &= bool(np.array_equal(lab, alone[pick[idx]][0]))
             span_srv = time.perf_counter() - t_start
             # sequential plain solves of the same arrival process
             lat_seq, t_start = [], time.perf_counter()

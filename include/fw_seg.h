@@ -243,17 +243,24 @@ typedef struct fw_graph {
 } fw_graph;
 
 enum { FW_SCHED_AUTO = 0, FW_SCHED_STATIC = 1, FW_SCHED_DYNAMIC = 2 };
+/* How a persistent launch is issued: directly; from a captured CUDA graph,
+ * with a failed capture an error (FW_ERR_CUDA); or from a captured graph when
+ * the stream can be captured, else directly (fw_batch_info says which). */
+enum { FW_GRAPH_OFF = 0, FW_GRAPH_REQUIRED = 1, FW_GRAPH_PREFERRED = 2 };
 
 typedef struct fw_batch_opts {
     int32_t weight_dtype;      /* FW_WEIGHTS_*, shared by every problem */
     int32_t blocks_per_sm;     /* 0: autotune (cached) */
-    int32_t schedule;          /* FW_SCHED_*: static grid stride or atomic work counter */
-    int32_t iters_per_launch;  /* 0: every iteration in one launch */
-    int32_t use_graph;         /* 1: capture the launch in a CUDA graph and replay it */
+    int32_t schedule;          /* FW_SCHED_*: static grid stride or atomic work counter
+                                  (AUTO: autotuned) */
+    int32_t iters_per_launch;  /* -1: autotune; 0: every iteration in one launch */
+    int32_t use_graph;         /* FW_GRAPH_* (default FW_GRAPH_REQUIRED) */
     int32_t spin_budget_ms;    /* bound on one grid-barrier wait */
     int32_t test_barrier_extra;/* test hook, keep 0: the barrier also waits for this many
                                   blocks that never arrive, so every wait runs out */
-    int32_t reserved;
+    int32_t lanes_per_row;     /* -1: autotune; 0: each problem's own count (from its
+                                  options, else its mean degree); else 1,2,4,..,32 for
+                                  every problem */
     const char *tune_cache;    /* autotune cache file; NULL: $FW_TUNE_CACHE or none */
     void *cuda_stream;         /* cudaStream_t; NULL: the batch makes one */
 } fw_batch_opts;
@@ -262,15 +269,34 @@ typedef struct fw_batch_info {
     int32_t grid;              /* blocks of the persistent launch */
     int32_t blocks_per_sm;
     int32_t schedule;          /* FW_SCHED_STATIC or FW_SCHED_DYNAMIC */
-    int32_t graph_captured;    /* 1 if the launch runs from a CUDA graph */
+    int32_t graph_captured;    /* 1 if the last launch ran from a captured CUDA graph */
     int32_t tuned;             /* 0 set by the caller, 1 measured now, 2 from the cache */
-    int32_t kmax;              /* class bound of the compiled kernel */
+    int32_t kmax;              /* class bound of the persistent kernel (>= the largest K) */
+    int32_t lanes_per_row;     /* lanes per CSR row of every problem; 0: each problem's
+                                  own count from its mean degree */
+    int32_t iters_per_launch;  /* 0: every iteration in one launch */
+    int32_t graph_error;       /* cudaError_t of the last failed capture, 0 if none */
+    int32_t reserved;
     double tune_ms;            /* time spent autotuning */
     size_t pool_bytes;         /* device bytes of the problem pool */
 } fw_batch_info;
 
 typedef struct fw_batch fw_batch;
 
+/* Defaults: FP32 weights; blocks per SM, schedule, lanes per row and
+ * iterations per launch autotuned; FW_GRAPH_REQUIRED; 2000 ms barrier budget.
+ *
+ * Autotuning (at create, when any of those four is left to it) times a few
+ * iterations of the batch itself, from U_0, for each candidate, one
+ * dimension after the other: blocks per SM x schedule; then lanes per CSR
+ * row (each problem's own count, or 1, 2, 4, 8 for all); then the class
+ * bound the persistent kernel is compiled for (the smallest one that holds
+ * the batch's largest K, or the next); then iterations per launch (all, 64
+ * or 16).  The schedule, the class bound and the launch length change no
+ * result; the lanes per row change the order in which a row's entries are
+ * summed, so a batch equals single solves bit for bit when those use the
+ * same lanes_per_row (fw_batch_info reports it).  The choice is cached in
+ * tune_cache under a signature of the device and the batch's sizes. */
 fw_status fw_batch_default_opts(fw_batch_opts *opts);
 
 /* Create a batch of P problems.  graphs[P] are host graphs, opts[P] their
@@ -297,10 +323,12 @@ void fw_batch_destroy(fw_batch *b);
  * wait in a FIFO queue; a request is admitted when a slot is free and its
  * device footprint fits in the free pool, uploaded and assembled on a side
  * stream while the current epoch runs, and joins the next epoch.  An epoch is
- * one persistent launch of iters_per_epoch iterations over every resident
- * request.  Requests that meet their stop rule are harvested (labels copied to
- * the host) and their memory is reused.  Results are bitwise the same as when
- * the request is solved alone.
+ * iters_per_epoch iterations of every resident request (four times as many
+ * while no request waits for admission): one persistent launch over all of
+ * them, or, when a single request is resident, the single-problem kernels of
+ * fw_seg_solve for it.  Requests that meet their stop rule are harvested
+ * (labels copied to the host) and their memory is reused.  Results are
+ * bitwise the same as when the request is solved alone.
  * ---------------------------------------------------------------------- */
 
 typedef struct fw_srv_opts {
@@ -342,6 +370,12 @@ fw_status fw_srv_poll(fw_srv *s, uint64_t ticket, int32_t *labels_host, fw_seg_s
 /* As fw_srv_poll, blocking up to timeout_ms (negative: no limit). */
 fw_status fw_srv_wait(fw_srv *s, uint64_t ticket, int32_t timeout_ms, int32_t *labels_host,
                       fw_seg_stats *stats);
+
+/* Block up to timeout_ms (negative: no limit) until some request has
+ * finished whose result has not been returned yet; FW_OK with its ticket
+ * (fetch the result with fw_srv_poll), or FW_PENDING when the time ran out.
+ * Each finished ticket is reported once, in completion order. */
+fw_status fw_srv_wait_any(fw_srv *s, int32_t timeout_ms, uint64_t *ticket);
 
 fw_status fw_srv_get_info(fw_srv *s, fw_srv_info *info);
 

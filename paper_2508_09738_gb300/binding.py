@@ -60,12 +60,15 @@ class fw_batch_opts(ctypes.Structure):
     _fields_ = [("weight_dtype", c_int32), ("blocks_per_sm", c_int32), ("schedule", c_int32),
                 ("iters_per_launch", c_int32), ("use_graph", c_int32),
                 ("spin_budget_ms", c_int32), ("test_barrier_extra", c_int32),
-                ("reserved", c_int32), ("tune_cache", ctypes.c_char_p), ("cuda_stream", c_void_p)]
+                ("lanes_per_row", c_int32), ("tune_cache", ctypes.c_char_p),
+                ("cuda_stream", c_void_p)]
 
 
 class fw_batch_info(ctypes.Structure):
     _fields_ = [("grid", c_int32), ("blocks_per_sm", c_int32), ("schedule", c_int32),
                 ("graph_captured", c_int32), ("tuned", c_int32), ("kmax", c_int32),
+                ("lanes_per_row", c_int32), ("iters_per_launch", c_int32),
+                ("graph_error", c_int32), ("reserved", c_int32),
                 ("tune_ms", c_double), ("pool_bytes", c_size_t)]
 
     def as_dict(self) -> dict:
@@ -91,6 +94,7 @@ class fw_srv_info(ctypes.Structure):
 
 
 SCHED = {"auto": 0, "static": 1, "dynamic": 2}
+GRAPH = {"off": 0, "required": 1, "preferred": 2}
 
 _lib = None
 
@@ -131,6 +135,7 @@ _SIGS = {
     "fw_srv_poll": (c_int32, [c_void_p, ctypes.c_uint64, c_void_p, POINTER(fw_seg_stats)]),
     "fw_srv_wait": (c_int32, [c_void_p, ctypes.c_uint64, c_int32, c_void_p,
                               POINTER(fw_seg_stats)]),
+    "fw_srv_wait_any": (c_int32, [c_void_p, c_int32, POINTER(ctypes.c_uint64)]),
     "fw_srv_get_info": (c_int32, [c_void_p, POINTER(fw_srv_info)]),
     "fw_srv_destroy": (None, [c_void_p]),
     "fw_energy_noalloc": (c_int32, [c_int64, c_int32, c_void_p, c_void_p, c_void_p, c_int64,
@@ -396,6 +401,8 @@ def fw_batch_default_opts(**kw) -> fw_batch_opts:
             v = WEIGHTS[v]
         if k == "schedule" and isinstance(v, str):
             v = SCHED[v]
+        if k == "use_graph" and isinstance(v, str):
+            v = GRAPH[v]
         if k == "tune_cache" and isinstance(v, str):
             v = v.encode()
         if k == "cuda_stream" and v is not None and not isinstance(v, int):
@@ -507,6 +514,8 @@ def fw_srv_default_opts(**kw) -> fw_srv_opts:
             v = WEIGHTS[v]
         if k == "schedule" and isinstance(v, str):
             v = SCHED[v]
+        if k == "use_graph" and isinstance(v, str):
+            v = GRAPH[v]
         if k == "cuda_stream" and v is not None and not isinstance(v, int):
             v = int(getattr(v, "cuda_stream", v))
         setattr(o, k, v)
@@ -547,6 +556,14 @@ def fw_srv_wait(s, ticket: int, n: int, timeout_ms: int = -1):
     return rc, lab, st
 
 
+def fw_srv_wait_any(s, timeout_ms: int = -1):
+    """(FW_OK, ticket) of a finished request not reported before, or
+    (FW_PENDING, None) when timeout_ms ran out."""
+    t = ctypes.c_uint64()
+    rc = _check(lib().fw_srv_wait_any(s, int(timeout_ms), ctypes.byref(t)))
+    return (rc, int(t.value)) if rc == FW_OK else (rc, None)
+
+
 def fw_srv_get_info(s) -> fw_srv_info:
     i = fw_srv_info()
     _check(lib().fw_srv_get_info(s, ctypes.byref(i)))
@@ -583,6 +600,9 @@ class Server:
 
     def wait(self, ticket, n, timeout_ms=-1):
         return fw_srv_wait(self.s, ticket, n, timeout_ms)
+
+    def wait_any(self, timeout_ms=-1):
+        return fw_srv_wait_any(self.s, timeout_ms)
 
     def info(self):
         return fw_srv_get_info(self.s)

@@ -170,11 +170,21 @@ public:
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_persistent<T, WT, KMAX>, kBlock,
                                                              smem());
     }
+    // Cooperative launch (all blocks co-resident, which the grid barrier
+    // needs) through the extensible launch API, which stream capture records
+    // as a cooperative kernel node.
     cudaError_t launch(const BatchArgs& a, int grid, cudaStream_t s) override {
-        BatchArgs args = a;
-        void* params[] = {&args};
-        return cudaLaunchCooperativeKernel((const void*)k_persistent<T, WT, KMAX>, dim3(grid),
-                                           dim3(kBlock), params, smem(), s);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(unsigned(grid));
+        cfg.blockDim = dim3(kBlock);
+        cfg.dynamicSmemBytes = smem();
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, k_persistent<T, WT, KMAX>, a);
     }
 };
 

@@ -134,7 +134,16 @@ public:
     GridBar* d_bar = nullptr;
     GridBar* h_bar = nullptr;      // pinned
     int sms = 0, occ = 0, bps = 0, grid = 0, schedule = FW_SCHED_DYNAMIC;
-    int use_graph = 1, graph_captured = 0, expect_extra = 0;
+    // use_graph: FW_GRAPH_OFF, FW_GRAPH_REQUIRED or FW_GRAPH_PREFERRED;
+    // graph_captured: 1 when the last launch ran from a captured graph;
+    // graph_error: the CUDA error of the last failed capture (0: none)
+    int use_graph = FW_GRAPH_REQUIRED, graph_captured = 0, graph_error = 0, expect_extra = 0;
+    int kmax_kern = 4;     // class bound of the persistent kernel (>= kmax)
+    int lanes_all = 0;     // lanes per row of every problem (0: each problem's own)
+    // serving: a lone live problem runs the single-problem kernels (slots then
+    // carry the 4-bit class array those kernels gather)
+    bool plain_path = false;
+    std::map<int, std::unique_ptr<Ops>> plain;   // per class bound
     long long budget = 0;
     cudaGraphExec_t graph = nullptr;
     int graph_iters = -1;
@@ -203,6 +212,7 @@ public:
             set_error("device does not support cooperative launches");
             return FW_ERR_UNSUPPORTED;
         }
+        kmax_kern = kmax;
         FW_CUDA(bk->occupancy(&occ));
         if (occ < 1) {
             set_error("persistent kernel cannot be resident");
@@ -214,6 +224,41 @@ public:
         budget = (long long)std::max(spin_ms, 1) * (long long)clock_khz;
         set_grid(blocks_per_sm > 0 ? blocks_per_sm : occ,
                  sched == FW_SCHED_STATIC ? FW_SCHED_STATIC : FW_SCHED_DYNAMIC);
+        return FW_OK;
+    }
+
+    // Persistent kernel compiled for class bound km >= kmax (the same
+    // arithmetic for every K <= kmax; only bin strides and guards differ).
+    fw_status set_kernel_kmax(int km) {
+        if (km == kmax_kern) return FW_OK;
+        std::unique_ptr<BatchKern> k(make_batch_kern(wd, km));
+        if (!k) return invalid("no persistent kernel for this class bound");
+        FW_CUDA(k->configure());
+        int o = 0;
+        FW_CUDA(k->occupancy(&o));
+        if (o < 1) {
+            set_error("persistent kernel cannot be resident");
+            return FW_ERR_UNSUPPORTED;
+        }
+        bk = std::move(k);
+        kmax_kern = km;
+        occ = o;
+        set_grid(std::min(bps, occ), schedule);
+        return FW_OK;
+    }
+
+    // Lanes per CSR row of every problem (0: each problem's planned count).
+    fw_status set_lanes(int L) {
+        lanes_all = L;
+        for (int s = 0; s < nslots(); ++s) {
+            Slot& sl = slots[size_t(s)];
+            if (!sl.used) continue;
+            sl.pd.lanes = L > 0 ? L : sl.lay.lanes;
+            FW_CUDA(cudaMemcpyAsync(d_desc + s, &sl.pd, sizeof(ProbDesc), cudaMemcpyHostToDevice,
+                                    stream));
+        }
+        FW_CUDA(cudaStreamSynchronize(stream));
+        invalidate_graph();
         return FW_OK;
     }
 
@@ -345,33 +390,93 @@ public:
             work_dirty = false;
         }
         const BatchArgs a = args(nlive, iters);
-        if (use_graph && (!graph || graph_iters != iters)) {
-            invalidate_graph();
-            cudaGraph_t g = nullptr;
-            bool ok = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
-            if (ok) {
-                cudaMemsetAsync(d_bar, 0, sizeof(GridBar), stream);
-                bk->launch(a, grid, stream);
-                ok = cudaStreamEndCapture(stream, &g) == cudaSuccess;
-                if (ok) ok = cudaGraphInstantiate(&graph, g, 0) == cudaSuccess;
-                if (g) cudaGraphDestroy(g);
+        bool from_graph = false;
+        if (use_graph != FW_GRAPH_OFF) {
+            if (!graph || graph_iters != iters) {
+                invalidate_graph();
+                cudaGraph_t g = nullptr;
+                cudaError_t e = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal);
+                if (e == cudaSuccess) {
+                    const cudaError_t e1 = cudaMemsetAsync(d_bar, 0, sizeof(GridBar), stream);
+                    const cudaError_t e2 = bk->launch(a, grid, stream);
+                    e = cudaStreamEndCapture(stream, &g);
+                    if (e == cudaSuccess) e = e1 != cudaSuccess ? e1 : e2;
+                    if (e == cudaSuccess) e = cudaGraphInstantiate(&graph, g, 0);
+                    if (g) cudaGraphDestroy(g);
+                }
+                cudaGetLastError();
+                if (e != cudaSuccess) {
+                    graph = nullptr;
+                    graph_captured = 0;
+                    graph_error = int(e);
+                    if (use_graph == FW_GRAPH_REQUIRED)
+                        return cuda_fail(e, "capturing the persistent launch in a CUDA graph "
+                                            "(use_graph = FW_GRAPH_PREFERRED allows direct "
+                                            "launches)");
+                } else {
+                    graph_iters = iters;
+                    graph_error = 0;
+                }
             }
-            cudaGetLastError();
-            graph_captured = ok ? 1 : 0;
-            if (!ok) {
-                graph = nullptr;
-                use_graph = 0;
-            } else {
-                graph_iters = iters;
+            if (graph) {
+                FW_CUDA(cudaGraphLaunch(graph, stream));
+                from_graph = true;
             }
         }
-        if (use_graph && graph) {
-            FW_CUDA(cudaGraphLaunch(graph, stream));
-        } else {
+        if (!from_graph) {
             FW_CUDA(cudaMemsetAsync(d_bar, 0, sizeof(GridBar), stream));
             FW_CUDA(bk->launch(a, grid, stream));
         }
+        graph_captured = from_graph ? 1 : 0;
         return FW_OK;
+    }
+
+    fw_status plain_ops(int K, Ops** out) {
+        const int km = kmax_for(K);
+        auto it = plain.find(km);
+        if (it == plain.end()) {
+            std::unique_ptr<Ops> o(make_ops(wd, K));
+            if (!o) return invalid("no kernels for this weight dtype / K");
+            FW_CUDA(o->configure());
+            it = plain.emplace(km, std::move(o)).first;
+        }
+        *out = it->second.get();
+        return FW_OK;
+    }
+
+    // One epoch of `iters` iterations.  With a single live problem (serving)
+    // they run as the single-problem kernels of fw_seg_solve: pass A with the
+    // previous decision fused in and pass B per iteration, one finish at the
+    // end -- the same arithmetic as the persistent kernel, in its faster
+    // compile-time forms, and without grid barriers.  The state either path
+    // leaves (decision committed, totals cleared) is the one the other starts
+    // from.  Otherwise the persistent launch over every live problem.
+    fw_status launch_epoch(int iters, int* nlive_out) {
+        if (plain_path) {
+            int live = -1, cnt = 0;
+            for (int s = 0; s < nslots(); ++s)
+                if (slots[size_t(s)].used && !h_state[s].done) {
+                    live = s;
+                    ++cnt;
+                }
+            if (cnt == 1) {
+                Ops* op = nullptr;
+                FW_TRY(plain_ops(slots[size_t(live)].lay.K, &op));
+                const ProbDesc& pd = slots[size_t(live)].pd;
+                ProbState* st = d_state + live;
+                FW_CUDA(cudaMemsetAsync(d_bar, 0, sizeof(GridBar), stream));
+                for (int i = 0; i < iters; ++i) {
+                    op->passA(pd, st, stream, i > 0 ? 1 : 0);
+                    op->passB(pd, st, stream);
+                }
+                op->finish(pd, st, stream);
+                FW_CUDA(cudaGetLastError());
+                graph_captured = 0;
+                *nlive_out = 1;
+                return FW_OK;
+            }
+        }
+        return launch(iters, nlive_out);
     }
 
     // Copy every slot's state and the barrier record back after a launch.
@@ -442,7 +547,7 @@ using namespace fw;
 
 static_assert(sizeof(fw_graph) == 48, "fw_graph ABI");
 static_assert(sizeof(fw_batch_opts) == 48, "fw_batch_opts ABI");
-static_assert(sizeof(fw_batch_info) == 40, "fw_batch_info ABI");
+static_assert(sizeof(fw_batch_info) == 56, "fw_batch_info ABI");
 static_assert(sizeof(fw_srv_opts) == 48, "fw_srv_opts ABI");
 static_assert(sizeof(fw_srv_info) == 72, "fw_srv_info ABI");
 
@@ -452,6 +557,7 @@ struct fw_batch {
     Engine eng;
     int P = 0;
     fw_batch_opts bo{};
+    int ipl = 0;            // iterations per launch in use (0: all in one)
     int max_iters = 0;
     int tuned = 0;
     double tune_ms = 0.0;
@@ -470,8 +576,10 @@ static std::string tune_signature(const fw_batch* b) {
     cudaGetDevice(&dev);
     cudaGetDeviceProperties(&p, dev);
     char buf[512];
-    std::snprintf(buf, sizeof(buf), "%s|wd%d|k%d|P%d|rows%lld|nnz%lld|tiles%lld", p.name,
-                  b->eng.wd, b->eng.kmax, b->P, (long long)rows, (long long)nnz, (long long)tiles);
+    std::snprintf(buf, sizeof(buf), "v2|%s|wd%d|k%d|P%d|rows%lld|nnz%lld|tiles%lld|want%d%d%d%d",
+                  p.name, b->eng.wd, b->eng.kmax, b->P, (long long)rows, (long long)nnz,
+                  (long long)tiles, b->bo.blocks_per_sm, b->bo.schedule, b->bo.lanes_per_row,
+                  b->bo.iters_per_launch);
     std::string s(buf);
     for (char& c : s)
         if (c == ' ') c = '_';
@@ -483,30 +591,37 @@ static const char* tune_path(const fw_batch* b) {
     return std::getenv("FW_TUNE_CACHE");
 }
 
-static bool tune_lookup(const fw_batch* b, const std::string& sig, int* bps, int* sched) {
+// A tuned configuration of the persistent launch.
+struct TuneChoice {
+    int bps = 0, sched = FW_SCHED_DYNAMIC, lanes = 0, kmax = 4, ipl = 0;
+};
+
+static bool tune_lookup(const fw_batch* b, const std::string& sig, TuneChoice* c) {
     const char* path = tune_path(b);
     if (!path) return false;
     FILE* f = std::fopen(path, "r");
     if (!f) return false;
-    char key[512];
-    int x = 0, y = 0;
+    char line[1024], key[600];
     bool found = false;
-    while (std::fscanf(f, "%511s %d %d", key, &x, &y) == 3)
-        if (sig == key) {
-            *bps = x;
-            *sched = y;
+    while (std::fgets(line, sizeof(line), f)) {
+        TuneChoice t;
+        if (std::sscanf(line, "%599s %d %d %d %d %d", key, &t.bps, &t.sched, &t.lanes, &t.kmax,
+                        &t.ipl) == 6 &&
+            sig == key) {
+            *c = t;
             found = true;
         }
+    }
     std::fclose(f);
     return found;
 }
 
-static void tune_store(const fw_batch* b, const std::string& sig, int bps, int sched) {
+static void tune_store(const fw_batch* b, const std::string& sig, const TuneChoice& c) {
     const char* path = tune_path(b);
     if (!path) return;
     FILE* f = std::fopen(path, "a");
     if (!f) return;
-    std::fprintf(f, "%s %d %d\n", sig.c_str(), bps, sched);
+    std::fprintf(f, "%s %d %d %d %d %d\n", sig.c_str(), c.bps, c.sched, c.lanes, c.kmax, c.ipl);
     std::fclose(f);
 }
 
@@ -521,62 +636,140 @@ static fw_status batch_reset(fw_batch* b) {
     return FW_OK;
 }
 
-// Autotune: blocks per SM x schedule, timed on a few iterations of the batch
-// itself; neither choice changes any problem's arithmetic.
+static fw_status apply_choice(fw_batch* b, const TuneChoice& c) {
+    Engine& e = b->eng;
+    FW_TRY(e.set_kernel_kmax(c.kmax));
+    e.set_grid(c.bps, c.sched);
+    FW_TRY(e.set_lanes(c.lanes));
+    b->ipl = c.ipl;
+    return FW_OK;
+}
+
+// Device time of `iters` iterations of the whole batch from U_0 in launches
+// of `per` iterations (0: one launch), best of two runs.
+static fw_status time_batch(fw_batch* b, int iters, int per, cudaEvent_t ev0, cudaEvent_t ev1,
+                            float* best) {
+    Engine& e = b->eng;
+    *best = 1e30f;
+    for (int rep = 0; rep < 2; ++rep) {
+        FW_TRY(batch_reset(b));
+        FW_CUDA(cudaEventRecord(ev0, e.stream));
+        int left = iters;
+        while (left > 0) {
+            const int it = per > 0 ? std::min(per, left) : left;
+            int nlive = 0;
+            FW_TRY(e.launch(it, &nlive));
+            if (nlive == 0) break;
+            FW_TRY(e.collect());
+            left -= it;
+        }
+        FW_CUDA(cudaEventRecord(ev1, e.stream));
+        FW_CUDA(cudaEventSynchronize(ev1));
+        float ms = 0.f;
+        FW_CUDA(cudaEventElapsedTime(&ms, ev0, ev1));
+        *best = std::min(*best, ms);
+    }
+    return FW_OK;
+}
+
+// Autotune the persistent launch (see fw_batch_default_opts): one dimension
+// after the other, each candidate timed on a few iterations of the batch
+// itself; the problems are reset to U_0 afterwards.
 static fw_status batch_tune(fw_batch* b) {
     Engine& e = b->eng;
-    std::vector<int> scheds;
-    if (b->bo.schedule == FW_SCHED_AUTO) scheds = {FW_SCHED_STATIC, FW_SCHED_DYNAMIC};
-    else scheds = {b->bo.schedule};
-    std::vector<int> grids;
-    if (b->bo.blocks_per_sm > 0) grids = {std::min(b->bo.blocks_per_sm, e.occ)};
-    else
-        for (int x = 1; x <= e.occ; ++x) grids.push_back(x);
+    const fw_batch_opts& o = b->bo;
     const std::string sig = tune_signature(b);
-    int bps = 0, sched = 0;
-    if (tune_lookup(b, sig, &bps, &sched)) {
-        e.set_grid(bps, sched);
+    TuneChoice c;
+    if (tune_lookup(b, sig, &c)) {
+        FW_TRY(apply_choice(b, c));
         b->tuned = 2;
-        return FW_OK;
+        return batch_reset(b);
     }
     const auto t0 = std::chrono::steady_clock::now();
-    cudaEvent_t ev0, ev1;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     FW_CUDA(cudaEventCreate(&ev0));
     FW_CUDA(cudaEventCreate(&ev1));
-    const int it = 4;
-    float best = 1e30f;
-    int bb = e.occ, bs = FW_SCHED_DYNAMIC;
+    struct EvGuard {
+        cudaEvent_t a, b;
+        ~EvGuard() {
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+        }
+    } guard{ev0, ev1};
     const int keep_graph = e.use_graph;
-    e.use_graph = 0;
-    for (int sc : scheds) {
-        for (int x : grids) {
-            e.set_grid(x, sc);
-            fw_status rc = batch_reset(b);
-            if (rc != FW_OK) return rc;
-            cudaEventRecord(ev0, e.stream);
-            rc = e.run(it);
-            cudaEventRecord(ev1, e.stream);
-            if (rc != FW_OK) {
-                cudaEventDestroy(ev0);
-                cudaEventDestroy(ev1);
-                return rc;
+    e.use_graph = FW_GRAPH_OFF;   // candidates change the launch; graphs come after
+    c.kmax = e.kmax;
+    c.lanes = std::max(0, o.lanes_per_row);
+    c.ipl = std::max(0, o.iters_per_launch);
+    c.sched = o.schedule == FW_SCHED_STATIC ? FW_SCHED_STATIC : FW_SCHED_DYNAMIC;
+    c.bps = o.blocks_per_sm > 0 ? std::min(o.blocks_per_sm, e.occ) : e.occ;
+    const int it = 4;
+    float best = 1e30f, ms = 0.f;
+    auto consider = [&](const TuneChoice& t, int iters, int per) -> fw_status {
+        FW_TRY(apply_choice(b, t));
+        FW_TRY(time_batch(b, iters, per, ev0, ev1, &ms));
+        if (ms < best) {
+            best = ms;
+            c = t;
+        }
+        return FW_OK;
+    };
+    // blocks per SM x schedule
+    {
+        std::vector<int> scheds;
+        if (o.schedule == FW_SCHED_AUTO) scheds = {FW_SCHED_STATIC, FW_SCHED_DYNAMIC};
+        else scheds = {c.sched};
+        std::vector<int> grids;
+        if (o.blocks_per_sm > 0) grids = {c.bps};
+        else
+            for (int x = 1; x <= e.occ; ++x) grids.push_back(x);
+        const TuneChoice base = c;
+        for (int sc : scheds)
+            for (int x : grids) {
+                TuneChoice t = base;
+                t.sched = sc;
+                t.bps = x;
+                FW_TRY(consider(t, it, 0));
             }
-            cudaEventSynchronize(ev1);
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, ev0, ev1);
-            if (ms < best) {
-                best = ms;
-                bb = x;
-                bs = sc;
-            }
+    }
+    // lanes per row
+    if (o.lanes_per_row < 0) {
+        const TuneChoice base = c;
+        best = 1e30f;
+        for (int L : {0, 1, 2, 4, 8}) {
+            TuneChoice t = base;
+            t.lanes = L;
+            FW_TRY(consider(t, it, 0));
         }
     }
-    cudaEventDestroy(ev0);
-    cudaEventDestroy(ev1);
+    // class bound of the compiled kernel: the smallest that holds K, or the next
+    {
+        const TuneChoice base = c;
+        best = 1e30f;
+        FW_TRY(consider(base, it, 0));
+        const int nxt = kmax_for(base.kmax + 1);
+        if (nxt > base.kmax) {
+            TuneChoice t = base;
+            t.kmax = nxt;
+            t.bps = std::min(t.bps, e.occ);   // re-clamped to the new kernel's occupancy
+            FW_TRY(consider(t, it, 0));
+        }
+    }
+    // iterations per launch: 32 iterations as one launch, or launches of 16
+    if (o.iters_per_launch < 0) {
+        const TuneChoice base = c;
+        best = 1e30f;
+        for (int per : {0, 64, 16}) {
+            TuneChoice t = base;
+            t.ipl = per;
+            FW_TRY(consider(t, 32, per));
+        }
+    }
     e.use_graph = keep_graph;
-    e.set_grid(bb, bs);
+    FW_TRY(apply_choice(b, c));
+    c.bps = e.bps;   // as clamped
     FW_TRY(batch_reset(b));
-    tune_store(b, sig, bb, bs);
+    tune_store(b, sig, c);
     b->tuned = 1;
     b->tune_ms =
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -591,9 +784,10 @@ fw_status fw_batch_default_opts(fw_batch_opts* o) {
     o->weight_dtype = FW_WEIGHTS_F32;
     o->blocks_per_sm = 0;
     o->schedule = FW_SCHED_AUTO;
-    o->iters_per_launch = 0;
-    o->use_graph = 1;
+    o->iters_per_launch = -1;
+    o->use_graph = FW_GRAPH_REQUIRED;
     o->spin_budget_ms = 2000;
+    o->lanes_per_row = -1;
     return FW_OK;
 }
 
@@ -603,6 +797,14 @@ fw_status fw_batch_create(fw_batch** out, int32_t P, const fw_graph* graphs,
         if (!out) return invalid("out is NULL");
         *out = nullptr;
         if (P < 1 || !graphs || !opts) return invalid("P >= 1 graphs and options are required");
+        if (bopts) {
+            const int L = bopts->lanes_per_row;
+            if (L < -1 || L > 32 || (L > 0 && (L & (L - 1)) != 0))
+                return invalid("lanes_per_row must be -1, 0 or a power of two <= 32");
+            if (bopts->iters_per_launch < -1) return invalid("iters_per_launch must be >= -1");
+            if (bopts->use_graph < FW_GRAPH_OFF || bopts->use_graph > FW_GRAPH_PREFERRED)
+                return invalid("bad use_graph");
+        }
         std::unique_ptr<fw_batch> b(new fw_batch());
         if (bopts) b->bo = *bopts;
         else fw_batch_default_opts(&b->bo);
@@ -639,7 +841,12 @@ fw_status fw_batch_create(fw_batch** out, int32_t P, const fw_graph* graphs,
             int slot = -1;
             FW_TRY(e.add(hg, o, lays[size_t(p)], &slot));
         }
-        if (b->bo.blocks_per_sm <= 0 || b->bo.schedule == FW_SCHED_AUTO) FW_TRY(batch_tune(b.get()));
+        b->ipl = std::max(0, b->bo.iters_per_launch);
+        if (b->bo.blocks_per_sm <= 0 || b->bo.schedule == FW_SCHED_AUTO ||
+            b->bo.lanes_per_row < 0 || b->bo.iters_per_launch < 0)
+            FW_TRY(batch_tune(b.get()));
+        else if (b->bo.lanes_per_row > 0)
+            FW_TRY(e.set_lanes(b->bo.lanes_per_row));
         *out = b.release();
         return FW_OK;
     } catch (const std::bad_alloc&) {
@@ -651,7 +858,7 @@ fw_status fw_batch_create(fw_batch** out, int32_t P, const fw_graph* graphs,
 fw_status fw_batch_solve(fw_batch* b, fw_seg_stats* stats) {
     if (!b) return invalid("batch is NULL");
     Engine& e = b->eng;
-    const int per = b->bo.iters_per_launch > 0 ? b->bo.iters_per_launch : b->max_iters + 1;
+    const int per = b->ipl > 0 ? b->ipl : b->max_iters + 1;
     cudaEvent_t ev0, ev1;
     FW_CUDA(cudaEventCreate(&ev0));
     FW_CUDA(cudaEventCreate(&ev1));
@@ -711,7 +918,11 @@ fw_status fw_batch_get_info(fw_batch* b, fw_batch_info* info) {
     info->schedule = b->eng.schedule;
     info->graph_captured = b->eng.graph_captured;
     info->tuned = b->tuned;
-    info->kmax = b->eng.kmax;
+    info->kmax = b->eng.kmax_kern;
+    info->lanes_per_row = b->eng.lanes_all;
+    info->iters_per_launch = b->ipl;
+    info->graph_error = b->eng.graph_error;
+    info->reserved = 0;
     info->tune_ms = b->tune_ms;
     info->pool_bytes = b->eng.ra.cap();
     return FW_OK;
@@ -753,6 +964,7 @@ struct fw_srv {
     std::condition_variable cv_work, cv_done;
     std::deque<std::unique_ptr<Request>> queue;
     std::unordered_map<uint64_t, Result> results;
+    std::deque<uint64_t> finished;   // tickets in completion order, for fw_srv_wait_any
     std::vector<uint64_t> slot_ticket;
     std::vector<int> slot_epochs;
     uint64_t next_ticket = 1;
@@ -784,6 +996,7 @@ void fw_srv::harvest() {
         if (r.status < 0) info.failed++;
         info.resident--;
         results[t] = std::move(r);
+        finished.push_back(t);
     }
     cv_done.notify_all();
 }
@@ -798,9 +1011,16 @@ void fw_srv::loop() {
                 cv_work.wait(lk, [&] { return stop || !queue.empty(); });
             if (stop) return;
         }
-        // start the epoch over the resident requests ...
+        // start the epoch over the resident requests (four times longer while
+        // no request waits for admission: a problem that stops early in it
+        // skips the rest at once, so a long epoch only delays admissions) ...
+        bool waiting = false;
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            waiting = !queue.empty();
+        }
         int nlive = 0;
-        fw_status rc = e.launch(so.iters_per_epoch, &nlive);
+        fw_status rc = e.launch_epoch(so.iters_per_epoch * (waiting ? 1 : 4), &nlive);
         // ... and admit queued requests (FIFO) while it runs: upload and
         // assembly go to the side stream, the pool range is taken in order
         for (;;) {
@@ -822,6 +1042,7 @@ void fw_srv::loop() {
                 r.done = true;
                 r.status = ra;
                 results[rq->ticket] = std::move(r);
+                finished.push_back(rq->ticket);
                 info.failed++;
                 info.completed++;
                 cv_done.notify_all();
@@ -848,6 +1069,7 @@ void fw_srv::loop() {
                 r.done = true;
                 r.status = rc;
                 results[slot_ticket[size_t(s)]] = std::move(r);
+                finished.push_back(slot_ticket[size_t(s)]);
                 e.remove(s);
                 info.failed++;
                 info.completed++;
@@ -888,7 +1110,8 @@ fw_status fw_srv_create(fw_srv** out, const fw_srv_opts* opts) {
             o.hbm_budget_bytes < 4096)
             return invalid("bad serving options");
         FW_CUDA(cudaGetDevice(&s->device));
-        s->eng.use_graph = 1;
+        s->eng.use_graph = FW_GRAPH_PREFERRED;
+        s->eng.plain_path = true;
         FW_TRY(s->eng.init(o.weight_dtype, o.max_K, o.hbm_budget_bytes, o.max_slots, o.cuda_stream,
                            o.spin_budget_ms > 0 ? o.spin_budget_ms : 2000, o.blocks_per_sm,
                            o.schedule == FW_SCHED_STATIC ? FW_SCHED_STATIC : FW_SCHED_DYNAMIC));
@@ -925,6 +1148,7 @@ fw_status fw_srv_submit(fw_srv* s, const fw_graph* g, const fw_seg_opts* opts, u
         std::unique_ptr<Request> rq(new Request());
         const HostGraph hg{g->n, g->row_ptr_host, g->col_host, g->w_host, g->K, g->labels_host};
         FW_TRY(plan_problem(hg, o, rq->lay));
+        rq->lay.cls4 = g->K <= 16;   // for the single-problem kernels of a lone request
         rq->bytes = s->eng.bytes_for(rq->lay, o);
         if (rq->bytes + 256 > s->eng.ra.cap()) {
             set_error("request can never fit the server's device pool");
@@ -989,6 +1213,23 @@ fw_status fw_srv_wait(fw_srv* s, uint64_t ticket, int32_t timeout_ms, int32_t* l
     else s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready);
     bool found = false;
     return take_result(s, ticket, labels_host, stats, lk, &found);
+}
+
+fw_status fw_srv_wait_any(fw_srv* s, int32_t timeout_ms, uint64_t* ticket) {
+    if (!s || !ticket) return invalid("bad arguments");
+    std::unique_lock<std::mutex> lk(s->mu);
+    // tickets already taken by poll / wait are skipped
+    auto ready = [&] {
+        while (!s->finished.empty() && !s->results.count(s->finished.front()))
+            s->finished.pop_front();
+        return !s->finished.empty();
+    };
+    if (timeout_ms < 0) s->cv_done.wait(lk, ready);
+    else s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready);
+    if (!ready()) return FW_PENDING;
+    *ticket = s->finished.front();
+    s->finished.pop_front();
+    return FW_OK;
 }
 
 fw_status fw_srv_get_info(fw_srv* s, fw_srv_info* info) {

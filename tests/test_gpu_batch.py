@@ -34,15 +34,24 @@ def solve_alone(g, weights, **opts):
 
 
 @pytest.mark.parametrize("weights", ["f32", "bf16"])
-@pytest.mark.parametrize("schedule,bps", [("static", 1), ("dynamic", 2), ("static", 0)])
-def test_batch_bitwise_equals_single(weights, schedule, bps):
+@pytest.mark.parametrize("schedule,bps,lanes", [("static", 1, 0), ("dynamic", 2, 4),
+                                                ("static", 0, -1)])
+def test_batch_bitwise_equals_single(weights, schedule, bps, lanes):
+    """Batched solves equal single solves bit for bit when both use the same
+    lanes per row (the batch's tuned or fixed count, reported by info())."""
     gs = mixed_problems(P=10, seed=3)
     iters = [30 + 7 * p for p in range(len(gs))]          # different caps per problem
     opts = [B.fw_seg_default_opts(max_iters=it, weight_dtype=weights) for it in iters]
-    with B.Batch(gs, opts, weight_dtype=weights, schedule=schedule, blocks_per_sm=bps) as b:
+    with B.Batch(gs, opts, weight_dtype=weights, schedule=schedule, blocks_per_sm=bps,
+                 lanes_per_row=lanes) as b:
         stats = b.solve()
+        info = b.info()
+        assert info.graph_captured == 1 and info.graph_error == 0
+        if lanes >= 0:
+            assert info.lanes_per_row == lanes
         for p, g in enumerate(gs):
-            U, lab, st = solve_alone(g, weights, max_iters=iters[p])
+            U, lab, st = solve_alone(g, weights, max_iters=iters[p],
+                                     lanes_per_row=info.lanes_per_row)
             assert np.array_equal(b.U(p), U), p
             assert np.array_equal(b.labels(p), lab), p
             assert stats[p].iters == st.iters and stats[p].status == st.status
@@ -52,13 +61,13 @@ def test_batch_bitwise_equals_single(weights, schedule, bps):
 def test_batch_relaunch_and_reset_reproduce():
     gs = mixed_problems(P=6, seed=5)
     opts = B.fw_seg_default_opts(max_iters=40)
-    with B.Batch(gs, opts, iters_per_launch=7) as b:
+    with B.Batch(gs, opts, iters_per_launch=7, lanes_per_row=0) as b:
         b.solve()
         U1 = [b.U(p) for p in range(len(gs))]
         b.reset()
         b.solve()
         U2 = [b.U(p) for p in range(len(gs))]
-    with B.Batch(gs, opts) as b:               # one launch for all iterations
+    with B.Batch(gs, opts, iters_per_launch=0, lanes_per_row=0) as b:   # one launch
         b.solve()
         U3 = [b.U(p) for p in range(len(gs))]
     for a, c, d in zip(U1, U2, U3):
@@ -83,7 +92,7 @@ def test_batch_independent_stop_rules():
             B.fw_seg_default_opts(eps=0.1, omega0=1e5, max_iters=50),      # one shot
             B.fw_seg_default_opts(max_iters=60, step_rule="armijo"),
             B.fw_seg_default_opts(max_iters=60, oracle="full")]
-    with B.Batch(gs, opts) as b:
+    with B.Batch(gs, opts, lanes_per_row=0) as b:
         stats = b.solve()
     for p, (g, o) in enumerate(zip(gs, opts)):
         with B.Segmenter(g, eps=o.eps, omega0=o.omega0, max_iters=o.max_iters,
@@ -94,7 +103,14 @@ def test_batch_independent_stop_rules():
     assert stats[1].iters == 3 and stats[2].iters == 0 and stats[3].iters == 1
 
 
+def _tuned(i):
+    return (i.blocks_per_sm, i.schedule, i.lanes_per_row, i.kmax, i.iters_per_launch)
+
+
 def test_batch_autotune_cache(tmp_path):
+    """The tuner searches blocks per SM x schedule, lanes per row, the
+    kernel's class bound and iterations per launch; a second batch of the
+    same sizes takes the cached choice and gives the same bits."""
     gs = mixed_problems(P=4, seed=11)
     cache = str(tmp_path / "tune.txt")
     opts = B.fw_seg_default_opts(max_iters=10)
@@ -106,10 +122,51 @@ def test_batch_autotune_cache(tmp_path):
         i2 = b.info()
         b.solve()
         U2 = b.U(0)
+        assert b.info().graph_captured == 1
     assert i1.tuned == 1 and i2.tuned == 2
-    assert (i1.blocks_per_sm, i1.schedule) == (i2.blocks_per_sm, i2.schedule)
+    assert _tuned(i1) == _tuned(i2)
+    assert i1.lanes_per_row in (0, 1, 2, 4, 8) and i1.iters_per_launch in (0, 64, 16)
+    bounds = [4, 8, 10, 12, 16, 32]
+    km = min(x for x in bounds if x >= max(g.K for g in gs))
+    assert i1.kmax in (km, bounds[bounds.index(km) + 1]) and i1.tune_ms > 0
     assert np.array_equal(U1, U2)
     assert os.path.getsize(cache) > 0
+
+
+@pytest.mark.parametrize("kmax_K", [3, 10])
+def test_batch_graph_capture_equals_direct_launches(kmax_K):
+    """The persistent launch runs from a captured CUDA graph by default
+    (FW_GRAPH_REQUIRED), and gives the same bits as direct launches."""
+    gs = W.batched_blobs(P=5, n_min=300, n_max=20_000, K_min=kmax_K, K_max=kmax_K, seed=17,
+                         n_scale=0.2)
+    opts = B.fw_seg_default_opts(max_iters=45)
+    kw = dict(blocks_per_sm=2, schedule="dynamic", lanes_per_row=0, iters_per_launch=16)
+    with B.Batch(gs, opts, use_graph="required", **kw) as a, \
+            B.Batch(gs, opts, use_graph="off", **kw) as d:
+        sa, sd = a.solve(), d.solve()
+        ia, idd = a.info(), d.info()
+        assert ia.graph_captured == 1 and ia.graph_error == 0
+        assert idd.graph_captured == 0
+        for p in range(len(gs)):
+            assert np.array_equal(a.U(p), d.U(p)), p
+            assert (sa[p].iters, sa[p].gap) == (sd[p].iters, sd[p].gap)
+
+
+def test_batch_bf16_agrees_with_oracle():
+    """Batched BF16 weights against the FP64 oracle on the same rounded
+    weights, per problem, at reduced sizes of the batched configuration:
+    label agreement and the final objective."""
+    gs = W.batched_blobs(P=6, n_min=1000, n_max=200_000, K_min=3, K_max=10, label_frac=0.02,
+                         seed=W.SEED0 + 3, n_scale=0.03)
+    with B.Batch(gs, B.fw_seg_default_opts(max_iters=200), weight_dtype="bf16") as b:
+        b.solve()
+        for p, g in enumerate(gs):
+            P = O.make_problem(g, 50.0, 1000.0, "bf16")
+            Uo, info = O.gfw_solve(P, max_iters=200)
+            assert agreement(b.labels(p), O.labels_from_U(Uo)) >= 0.999, p
+            E = O.energy(b.U(p), P)
+            Eo = O.energy(Uo, P)
+            assert abs(E - Eo) <= 1e-4 * abs(Eo), (p, E, Eo)
 
 
 def test_batch_barrier_timeout_is_reported_and_recoverable():
@@ -118,7 +175,8 @@ def test_batch_barrier_timeout_is_reported_and_recoverable():
     gs = mixed_problems(P=3, seed=13)
     t0 = time.time()
     with B.Batch(gs, B.fw_seg_default_opts(max_iters=5), test_barrier_extra=1,
-                 spin_budget_ms=20, blocks_per_sm=1, schedule="static") as b:
+                 spin_budget_ms=20, blocks_per_sm=1, schedule="static", lanes_per_row=0,
+                 iters_per_launch=0) as b:
         with pytest.raises(B.FwError) as e:
             b.solve()
     assert e.value.status == B.FW_ERR_TIMEOUT
@@ -190,3 +248,35 @@ def test_server_rejects_and_reports_errors():
         assert rc == B.FW_NOT_CONVERGED and st.iters == 20
         info = srv.info()
         assert info.rejected == 2 and info.failed == 1
+
+
+def test_server_lone_requests_and_wait_any():
+    """Requests submitted one at a time run alone on the server (the
+    single-problem kernels); a burst then runs in the persistent kernel.
+    wait_any reports every finished ticket once, and every result equals
+    the request solved alone, bit for bit."""
+    reqs = requests(seed=33)[:8]
+    alone = [solve_alone(g, "f32", **o) for g, o in reqs]
+    with B.Server(hbm_budget_bytes=1 << 30, max_slots=8, max_K=8, iters_per_epoch=8) as srv:
+        for (g, o), (U, lab, st) in zip(reqs[:4], alone[:4]):      # one at a time
+            t = srv.submit(g, **o)
+            rc, tk = srv.wait_any(60_000)
+            assert rc == B.FW_OK and tk == t
+            rc, lab_s, st_s = srv.poll(t, g.n)
+            assert rc == st.status and np.array_equal(lab_s, lab)
+            assert st_s.iters == st.iters and st_s.gap == st.gap
+        tickets = {srv.submit(g, **o): k for k, (g, o) in enumerate(reqs[4:], start=4)}
+        seen = set()
+        while len(seen) < len(tickets):
+            rc, tk = srv.wait_any(60_000)
+            assert rc == B.FW_OK and tk in tickets and tk not in seen
+            seen.add(tk)
+            k = tickets[tk]
+            g, _ = reqs[k]
+            U, lab, st = alone[k]
+            rc, lab_s, st_s = srv.poll(tk, g.n)
+            assert rc == st.status and np.array_equal(lab_s, lab), k
+            assert st_s.iters == st.iters and st_s.gap == st.gap, k
+        assert srv.wait_any(10) == (B.FW_PENDING, None)
+        info = srv.info()
+    assert info.completed == len(reqs) and info.failed == 0
