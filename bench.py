@@ -823,6 +823,19 @@ def arm_record(args, arm, g, c, weights, iters, world, peaks):
         rec.update(compare_golden(gold, arm["labels"], arm["E"], arm["traj"], g.truth))
     else:
         rec["accuracy_vs_truth"] = {"gpu": float(np.mean(arm["labels"] == g.truth))}
+    g32, g64 = golden(args.workload, iters, "f32"), golden(args.workload, iters, "f64")
+    if g64 is not None and int(g64["nnz"]) == g.nnz:
+        rec["label_agreement_vs_unrounded_weights_oracle"] = float(
+            np.mean(arm["labels"] == g64["labels"].astype(np.int32)))
+        if g32 is not None:
+            # the oracle against itself: its run on FP32-rounded weights vs its
+            # run on the unrounded weights (a rounding-level input change)
+            ctl = {"label_agreement": float(np.mean(g32["labels"] == g64["labels"]))}
+            for k in ("gap", "q", "alpha", "E"):
+                m = min(len(g32[k]), len(g64[k]))
+                ctl[k + "_max_rel"] = float(np.max(np.abs(g32[k][:m] - g64[k][:m]) /
+                                                   np.abs(g64[k][:m])))
+            rec["oracle_rounding_control"] = ctl
     return rec
 
 

@@ -110,20 +110,56 @@ def test_free_running_blobs2k_agreement(blobs2k, weights):
         assert a == 1.0
 
 
-def test_free_running_sbm200k_vs_stored_oracle():
-    gold = np.load(os.path.join(HERE, "golden", "sbm200k_oracle500_f32.npz"))
-    c = W.CONFIGS["sbm200k"]
-    g = W.make_config_graph("sbm200k")
+def _control(workload, iters):
+    """The oracle's own sensitivity to a rounding-level change of its input:
+    its stored run on FP32-rounded weights against its stored run on the
+    unrounded FP64 weights (relative change about 6e-8 per weight).  Returns
+    the label disagreement and the largest relative change of g, q, alpha
+    and E over the trajectory."""
+    a = np.load(os.path.join(HERE, "golden", f"{workload}_oracle{iters}_f32.npz"))
+    b = np.load(os.path.join(HERE, "golden", f"{workload}_oracle{iters}_f64.npz"))
+    out = {"labels": float(np.mean(a["labels"] != b["labels"]))}
+    for k in ("gap", "q", "alpha", "E"):
+        out[k] = float(np.max(np.abs(a[k] - b[k]) / np.abs(b[k])))
+    return out
+
+
+@pytest.mark.parametrize("workload,weights", [("sbm200k", "f32"), ("voronoi2048", "f32"),
+                                              ("voronoi2048", "bf16")])
+def test_free_running_trajectory_vs_stored_oracle(workload, weights):
+    """Whole free-running trajectories at full size against the stored FP64
+    oracle run on the same rounded weights: g_k, q_k, alpha_k at every
+    iteration, E_{k+1} by the recurrence, the final labels and the directly
+    evaluated final objective.  The trajectory amplifies rounding-level
+    differences: the oracle's own runs on FP32-rounded and on unrounded
+    weights differ by 1e-3..4e-2 in q and alpha and in 0.16% of the image's
+    labels.  The GPU must stay within twice that control, per quantity."""
+    c = W.CONFIGS[workload]
+    gold = np.load(os.path.join(HERE, "golden", f"{workload}_oracle{c['iters']}_{weights}.npz"))
+    ctl = _control(workload, c["iters"])
+    g = W.make_config_graph(workload)
     assert int(gold["nnz"]) == g.nnz
-    with B.Segmenter(g, eps=c["eps"], omega0=c["omega0"], weight_dtype="f32",
+    with B.Segmenter(g, eps=c["eps"], omega0=c["omega0"], weight_dtype=weights,
                      max_iters=c["iters"]) as s:
-        st = s.solve()
+        traj = []
+        for _ in range(c["iters"] + 1):
+            st = s.step(1)
+            traj.append((st.gap, st.q, st.alpha, st.objective))
+            if st.status != B.FW_PENDING:
+                break
         lab = s.labels()
         E = s.objective()
-    assert st.iters == int(gold["iters"])
-    a = agreement(lab, gold["labels"])
-    assert a >= 0.999, a
-    assert rel(E, float(gold["energy"])) <= 1e-4
+    m = c["iters"]
+    assert st.iters == m == int(gold["iters"]) and st.status == B.FW_NOT_CONVERGED
+    t = np.array(traj[:m])
+    ref = {"gap": gold["gap"][:m], "q": gold["q"][:m], "alpha": gold["alpha"][:m],
+           "E": gold["E"][1:m + 1]}
+    for col, k in enumerate(("gap", "q", "alpha", "E")):
+        err = np.max(np.abs(t[:, col] - ref[k]) / np.abs(ref[k]))
+        assert err <= 2.0 * ctl[k], (k, err, ctl[k])
+    dis = float(np.mean(lab != gold["labels"]))
+    assert dis <= 2.0 * max(ctl["labels"], 1e-6), (dis, ctl["labels"])
+    assert rel(E, float(gold["energy"])) <= 2.0 * ctl["E"]
 
 
 # ------------------------------------------------------------- one shot --
