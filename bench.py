@@ -115,14 +115,22 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------- byte counting --
-def bytes_per_unit(n, nnz, K, wbytes, tbytes=4):
+def column_bytes(g) -> int:
+    """Bytes per stored column index: the library keeps 16-bit offsets j - i
+    when every |j - i| < 2^15 (banded graphs such as pixel grids)."""
+    rows = np.repeat(np.arange(g.n, dtype=np.int64), np.diff(g.row_ptr))
+    far = g.nnz and int(np.max(np.abs(g.col.astype(np.int64) - rows))) >= 32768
+    return 4 if far else 2
+
+
+def bytes_per_unit(n, nnz, K, wbytes, tbytes=4, cbytes=4):
     """Algorithmic bytes of one FW iteration (the method's minimum: U and L U
     read and written, the CSR once, row_ptr, choice and fidelity bytes) and of
     each pass of the two-pass design (pass A: U, L U, L S in, U, L U out;
     pass B: U in for the moved rows, L S out, the CSR, row_ptr, the row's own
     choice and the gathered neighbour classes)."""
     row_pass = 5 * tbytes * n * K + 3 * n                 # U, LU, LS in; U, LU out; choice, fid
-    csr_pass = (2 * tbytes * n * K + (4 + wbytes) * nnz   # U in, LS out; col + weights
+    csr_pass = (2 * tbytes * n * K + (cbytes + wbytes) * nnz   # U in, LS out; col + weights
                 + 4 * (n + 1) + 2 * n)                    # row_ptr; choice of the row + gathers
     iteration = 4 * tbytes * n * K + (4 + wbytes) * nnz + 4 * n + 3 * n
     return dict(row_pass=row_pass, csr_pass=csr_pass, iteration=iteration)
@@ -616,7 +624,7 @@ def run_oneshot(args, rank, world, local):
     lab_gfw = seg.labels()
     seg.close()
     wb = {"f32": 4, "bf16": 2, "f64": 8}[weights]
-    nbytes = 4 * (g.n + 1) + (4 + wb) * g.nnz + g.n + 4 * g.n
+    nbytes = 4 * (g.n + 1) + (column_bytes(g) + wb) * g.nnz + g.n + 4 * g.n
     mean_ms = float(np.mean(kms))
     peaks = load_peaks()
     achieved = nbytes / (mean_ms / 1000.0) / 1e9
@@ -742,7 +750,7 @@ def compare_golden(gold, labels, E_gpu, traj, truth):
 def roofline_of(prof, g, weights, workload, peaks):
     wb = {"f32": 4, "bf16": 2, "f64": 8}[weights]
     tb = 8 if weights == "f64" else 4
-    by = bytes_per_unit(g.n, g.nnz, g.K, wb, tb)
+    by = bytes_per_unit(g.n, g.nnz, g.K, wb, tb, column_bytes(g))
     dom = "csr_pass" if prof["pass_b"] >= prof["pass_a"] else "row_pass"
     dom_ms = prof["pass_b"] if dom == "csr_pass" else prof["pass_a"]
     kernel = {"csr_pass": "k_passB", "row_pass": "k_passA"}[dom]

@@ -82,7 +82,8 @@ typedef struct fw_seg_opts {
     int32_t refresh_every;    /* recompute L U from scratch every R iterations (0: never) */
     int32_t iters_per_launch; /* iterations captured in one CUDA graph launch (>= 1) */
     int32_t lanes_per_row;    /* lanes per CSR row in the sparse passes: 0 (auto) or 1,2,4,..,32 */
-    int32_t reserved;
+    int32_t index_width;      /* stored column indices: 0 (auto: 16-bit offsets j - i when every
+                                 |j - i| < 2^15, as in pixel grids; else 32-bit) or 32 */
     void *cuda_stream;        /* cudaStream_t for all work; NULL: the handle makes one */
 } fw_seg_opts;
 
@@ -103,7 +104,8 @@ typedef struct fw_seg fw_seg;
 
 /* Fill *opts with defaults: eps 50, omega0 1000 (the paper's network values,
  * Sec. 5.2), gap_tol 0, FW_TOL_ABS, max_iters 500, FP32 weights, L_s, greedy
- * oracle, exact step, refresh_every 0, iters_per_launch 32, lanes auto. */
+ * oracle, exact step, refresh_every 0, iters_per_launch 32, lanes auto,
+ * index width auto. */
 fw_status fw_seg_default_opts(fw_seg_opts *opts);
 
 /* Device bytes a handle needs for a graph of n nodes, nnz stored entries and

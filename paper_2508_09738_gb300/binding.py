@@ -38,7 +38,7 @@ class fw_seg_opts(ctypes.Structure):
                 ("max_iters", c_int32), ("tol_mode", c_int32), ("weight_dtype", c_int32),
                 ("laplacian", c_int32), ("oracle", c_int32), ("step_rule", c_int32),
                 ("refresh_every", c_int32), ("iters_per_launch", c_int32),
-                ("lanes_per_row", c_int32), ("reserved", c_int32), ("cuda_stream", c_void_p)]
+                ("lanes_per_row", c_int32), ("index_width", c_int32), ("cuda_stream", c_void_p)]
 
 
 class fw_seg_stats(ctypes.Structure):

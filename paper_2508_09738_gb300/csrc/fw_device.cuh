@@ -870,6 +870,8 @@ __device__ __forceinline__ void csr_bins(const ProbDesc& pd, const T* __restrict
     const int64_t np = pd.npad;
     const int32_t* __restrict__ rp = pd.rp;
     const int32_t* __restrict__ col = pd.col;
+    const int16_t* __restrict__ col16 = reinterpret_cast<const int16_t*>(pd.col);
+    const bool c16 = pd.col16 != 0;   // uniform over the launch's problem
     const WT* __restrict__ val = static_cast<const WT*>(pd.val);
     const uint8_t* __restrict__ choice = pd.choice;
     const int tid = threadIdx.x;
@@ -896,15 +898,27 @@ __device__ __forceinline__ void csr_bins(const ProbDesc& pd, const T* __restrict
                 const bool two = e2 < e1;
                 int cc[8];
                 T v[8];
-                {
+                if (c16) {
+                    // four 16-bit offsets j - r in 8 bytes, sign-extended
+                    const uint2 c = ld_stream(reinterpret_cast<const uint2*>(col16 + e));
+                    cc[0] = r + (int(c.x << 16) >> 16); cc[1] = r + (int(c.x) >> 16);
+                    cc[2] = r + (int(c.y << 16) >> 16); cc[3] = r + (int(c.y) >> 16);
+                    if (two) {
+                        const uint2 d = ld_stream(reinterpret_cast<const uint2*>(col16 + e2));
+                        cc[4] = r + (int(d.x << 16) >> 16); cc[5] = r + (int(d.x) >> 16);
+                        cc[6] = r + (int(d.y << 16) >> 16); cc[7] = r + (int(d.y) >> 16);
+                    } else {
+                        cc[4] = cc[5] = cc[6] = cc[7] = r;
+                    }
+                } else {
                     const int4 c = ld_stream(reinterpret_cast<const int4*>(col + e));
                     cc[0] = c.x; cc[1] = c.y; cc[2] = c.z; cc[3] = c.w;
-                }
-                if (two) {
-                    const int4 c = ld_stream(reinterpret_cast<const int4*>(col + e2));
-                    cc[4] = c.x; cc[5] = c.y; cc[6] = c.z; cc[7] = c.w;
-                } else {
-                    cc[4] = cc[5] = cc[6] = cc[7] = r;
+                    if (two) {
+                        const int4 d = ld_stream(reinterpret_cast<const int4*>(col + e2));
+                        cc[4] = d.x; cc[5] = d.y; cc[6] = d.z; cc[7] = d.w;
+                    } else {
+                        cc[4] = cc[5] = cc[6] = cc[7] = r;
+                    }
                 }
                 if constexpr (sizeof(WT) == 2) {
                     float vf[4];

@@ -49,7 +49,7 @@ public:
     virtual void oneshot(const ProbDesc& pd, int32_t* labels, cudaStream_t s) = 0;
     virtual void build(int64_t n, const int32_t* rp, const int32_t* col, const double* w,
                        const double* deg, const int32_t* rpp, int32_t* colp, void* valp,
-                       void* diag, int comb, cudaStream_t s) = 0;
+                       void* diag, int comb, int col16, cudaStream_t s) = 0;
     virtual void reinit(const ProbDesc& pd, cudaStream_t s) = 0;
     virtual void labels(const ProbDesc& pd, int32_t* out, cudaStream_t s) = 0;
     virtual void objective(const ProbDesc& pd, const void* LUf, double* part, cudaStream_t s) = 0;
@@ -86,6 +86,8 @@ struct ProbLayout {
     // keep the 4-bit class array (ProbDesc::cls4): set by the two-kernel
     // single-problem path for K <= 16; the persistent kernels do not use it
     bool cls4 = false;
+    // store columns as 16-bit offsets when the graph allows (fw_seg_opts::index_width)
+    bool allow16 = true;
 };
 
 // Host checks (options, row_ptr, labels) and the padded layout.
@@ -136,10 +138,11 @@ fw_status upload_inputs(const HostGraph& g, Upload& up);
 // Upload, validate and build the problem into pd's arrays; U_0, L U_0 and the
 // fresh state *st.  Temporaries are stream-ordered (pool_alloc).  Waits
 // for the validation result on `s`.
-fw_status assemble_problem(Ops* ops, const HostGraph& g, const ProbLayout& lay, const ProbDesc& pd,
+fw_status assemble_problem(Ops* ops, const HostGraph& g, const ProbLayout& lay, ProbDesc& pd,
                            ProbState* st, cudaStream_t s);
 // The same from inputs already uploaded (or in flight) on stream s.
-fw_status assemble_uploaded(Ops* ops, Upload& up, const ProbLayout& lay, const ProbDesc& pd,
+// Sets pd.col16 from the validated graph.
+fw_status assemble_uploaded(Ops* ops, Upload& up, const ProbLayout& lay, ProbDesc& pd,
                             ProbState* st, cudaStream_t s);
 // Restart pd at U_0 (or at its current U when from_current) with a fresh state.
 fw_status restart_problem(Ops* ops, const ProbDesc& pd, ProbState* st, bool from_current,

@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(kBlock) k_state_init(ProbState* st, const doub
 template <typename WT, typename T>
 __global__ void k_build(int64_t n, const int32_t* rp, const int32_t* col, const double* w,
                         const double* deg, const int32_t* rpp, int32_t* colp, WT* valp, T* diag,
-                        int comb) {
+                        int comb, int col16) {
     // deg holds d_i for L = D - W and d_i^{-1/2} for L_s (k_inv_sqrt): the
     // normalised weight is then two FP64 products per entry, since FP64
     // square roots and divisions per entry dominated this kernel on GB300
@@ -300,10 +300,12 @@ __global__ void k_build(int64_t n, const int32_t* rp, const int32_t* col, const 
     int p = rpp[i];
     const int pend = rpp[i + 1];
     const double di = deg[i];
+    int16_t* colp16 = reinterpret_cast<int16_t*>(colp);
     for (int e = e0; e < e1; ++e, ++p) {
         const int j = col[e];
         const double x = comb ? w[e] : (w[e] * di) * deg[j];
-        colp[p] = j;
+        if (col16) colp16[p] = int16_t(j - int(i));   // |j - i| < 2^15 (checked)
+        else colp[p] = j;
         if constexpr (sizeof(WT) == 2)
             valp[p] = __float2bfloat16_rn(__double2float_rn(x));
         else if constexpr (sizeof(WT) == 4)
@@ -312,7 +314,8 @@ __global__ void k_build(int64_t n, const int32_t* rp, const int32_t* col, const 
             valp[p] = x;
     }
     for (; p < pend; ++p) {
-        colp[p] = int32_t(i);
+        if (col16) colp16[p] = 0;
+        else colp[p] = int32_t(i);
         valp[p] = WT(0.0f);
     }
     if (comb) diag[i] = T(di);

@@ -122,10 +122,10 @@ public:
     }
     void build(int64_t n, const int32_t* rp, const int32_t* col, const double* w,
                const double* deg, const int32_t* rpp, int32_t* colp, void* valp, void* diag,
-               int comb, cudaStream_t s) override {
+               int comb, int col16, cudaStream_t s) override {
         const unsigned g = unsigned((n + kBlock - 1) / kBlock);
         k_build<WT, T><<<g, kBlock, 0, s>>>(n, rp, col, w, deg, rpp, colp, (WT*)valp, (T*)diag,
-                                             comb);
+                                             comb, col16);
     }
     void reinit(const ProbDesc& pd, cudaStream_t s) override {
         k_reinit<T><<<rows_grid(pd), kBlock, 0, s>>>(pd);

@@ -21,14 +21,15 @@ namespace fw {
 // Validation and degrees of the input CSR (one thread per row):
 //   columns strictly increasing and in range, no self loop, w finite and >= 0,
 //   w_ij == w_ji (binary search in row j), d_i = sum_j w_ij > 0 (Sec. 1).
-// err bits: 1 graph structure / weights, 2 asymmetric, 4 isolated node.
+// err bits: 1 graph structure / weights, 2 asymmetric, 4 isolated node,
+// 8 (not an error) some |j - i| >= 2^15, so 16-bit column offsets cannot hold it.
 __global__ void k_validate(int64_t n, const int32_t* rp, const int32_t* col, const double* w,
                            double* deg, int* err) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int e0 = rp[i], e1 = rp[i + 1];
     double d = 0.0;
-    int bad = 0;
+    int bad = 0, far = 0;
     int prev = -1;
     for (int e = e0; e < e1; ++e) {
         const int j = col[e];
@@ -39,6 +40,7 @@ __global__ void k_validate(int64_t n, const int32_t* rp, const int32_t* col, con
         }
         prev = j;
         d += x;
+        far |= (j - int(i) > 32767) | (int(i) - j > 32767);
         int lo = rp[j], hi = rp[j + 1] - 1, pos = -1;
         while (lo <= hi) {
             const int mid = (lo + hi) >> 1;
@@ -54,7 +56,7 @@ __global__ void k_validate(int64_t n, const int32_t* rp, const int32_t* col, con
     }
     if (!bad && !(d > 0.0)) bad |= 4;
     deg[i] = d;
-    if (bad) atomicOr(err, bad);
+    if (bad | far) atomicOr(err, bad | (far ? 8 : 0));
 }
 
 __global__ void __launch_bounds__(kBlock) k_state_init(ProbState* st, const double* part, int nb) {
@@ -239,6 +241,7 @@ fw_status check_opts(const fw_seg_opts& o) {
     if (o.refresh_every < 0) return invalid("refresh_every must be >= 0");
     if (o.iters_per_launch < 1 || o.iters_per_launch > 4096)
         return invalid("iters_per_launch must be in [1, 4096]");
+    if (o.index_width != 0 && o.index_width != 32) return invalid("index_width must be 0 or 32");
     const int L = o.lanes_per_row;
     if (L != 0 && (L < 1 || L > 32 || (L & (L - 1)) != 0))
         return invalid("lanes_per_row must be 0 or a power of two <= 32");
@@ -324,6 +327,7 @@ fw_status plan_problem(const HostGraph& g, const fw_seg_opts& o, ProbLayout& lay
     lay.tile_rows = tile_rows_for(n);
     lay.ntiles = int32_t((n + lay.tile_rows - 1) / lay.tile_rows);
     lay.lanes = o.lanes_per_row ? o.lanes_per_row : default_lanes(double(acc) / double(n));
+    lay.allow16 = o.index_width != 32;
     return FW_OK;
 }
 
@@ -501,7 +505,7 @@ fw_status upload_inputs(const HostGraph& g, Upload& up) {
     return FW_OK;
 }
 
-fw_status assemble_problem(Ops* ops, const HostGraph& g, const ProbLayout& lay, const ProbDesc& pd,
+fw_status assemble_problem(Ops* ops, const HostGraph& g, const ProbLayout& lay, ProbDesc& pd,
                            ProbState* st, cudaStream_t s) {
     Upload up(s);
     FW_TRYS(check_graph_args(g));
@@ -509,7 +513,7 @@ fw_status assemble_problem(Ops* ops, const HostGraph& g, const ProbLayout& lay, 
     return assemble_uploaded(ops, up, lay, pd, st, s);
 }
 
-fw_status assemble_uploaded(Ops* ops, Upload& up, const ProbLayout& lay, const ProbDesc& pd,
+fw_status assemble_uploaded(Ops* ops, Upload& up, const ProbLayout& lay, ProbDesc& pd,
                             ProbState* st, cudaStream_t s) {
     Temps& t = up.t;
     const int64_t n = lay.n;
@@ -551,9 +555,12 @@ fw_status assemble_uploaded(Ops* ops, Upload& up, const ProbLayout& lay, const P
         set_error("graph: a node has degree 0");
         return FW_ERR_ISOLATED;
     }
+    // banded graphs (pixel grids, meshes) keep 16-bit column offsets: the
+    // same entries in half the column bytes of every sparse pass
+    pd.col16 = (lay.allow16 && !(err & 8)) ? 1 : 0;
     if (!pd.comb) k_inv_sqrt<<<gr, kBlock, 0, s>>>(n, d_deg);
     ops->build(n, d_rp, d_col, d_w, d_deg, pd.rp, const_cast<int32_t*>(pd.col),
-               const_cast<void*>(pd.val), const_cast<void*>(pd.diag), pd.comb, s);
+               const_cast<void*>(pd.val), const_cast<void*>(pd.diag), pd.comb, pd.col16, s);
     k_fid<<<gr, kBlock, 0, s>>>(n, d_lab, const_cast<int8_t*>(pd.fid));
     FW_TRYS(launched("build kernels"));
     return restart_problem(ops, pd, st, false, s);

@@ -33,7 +33,8 @@ static_assert(kAccWords <= kAccBank, "accumulator bank overflows its 128 bytes")
 // rows issues one coalesced 128-byte access.
 struct ProbDesc {
     const int32_t* rp;   // padded row_ptr [n+1] (entries start on multiples of 4)
-    const int32_t* col;  // padded columns [nnz_pad] (padding: the row itself)
+    const int32_t* col;  // padded columns [nnz_pad] (padding: the row itself); with col16
+                         // the same entries as int16 offsets j - i (padding: 0)
     const void* val;     // padded weights WT[nnz_pad] (padding: 0)
     const void* diag;    // T[n], combinatorial Laplacian only (else unused)
     void* U;             // T[K][npad]
@@ -56,7 +57,7 @@ struct ProbDesc {
     int32_t step_rule;   // 0 exact, 1 Armijo
     int32_t tol_mode;    // 0 abs, 1 relative to g_0
     int32_t max_iters;
-    int32_t pad_;
+    int32_t col16;       // 1: col holds 16-bit offsets (every |j - i| < 2^15)
     double inv_eps;      // 1/eps (0 when eps = +inf)
     double omega0;       // fidelity weight
     double gap_tol;

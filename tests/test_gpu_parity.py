@@ -449,6 +449,27 @@ def test_large_input_errors_on_upload_first_path():
         B.fw_seg_destroy(h)
 
 
+@pytest.mark.parametrize("weights", ["f32", "bf16", "f64"])
+def test_16bit_column_offsets_equal_32bit_indices(weights):
+    """A pixel grid is banded (every |j - i| < 2^15), so its columns are stored
+    as 16-bit offsets from the row by default; forcing 32-bit indices
+    (index_width = 32) gives bitwise the same iterates, statistics, one-shot
+    labels and SpMM refresh, on a ragged image (rows of 3, 5 and 8 entries)."""
+    g = W.voronoi_image(side=333, height=97, K=5, label_frac=0.01, seed=23)
+    out = []
+    for iw in (0, 32):
+        with B.Segmenter(g, weight_dtype=weights, max_iters=60, iters_per_launch=16,
+                         index_width=iw, omega0=1e5) as s:
+            lab1, _ = s.oneshot()
+            st = s.solve()
+            s.refresh()
+            G, ch, _ = s.grad()
+            out.append((s.U(), s.labels(), lab1, G, ch, st.iters, st.gap, st.objective))
+    a, b = out
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
 def test_deterministic_bitwise(blobs2k):
     outs = []
     for _ in range(2):

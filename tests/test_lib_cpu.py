@@ -88,6 +88,10 @@ def test_invalid_arguments_rejected_before_device_use(libpath):
         Bd.fw_seg_create(2, rp, col, w, 3, np.array([0, -1], np.int32),
                          Bd.fw_seg_default_opts(eps=-1.0))
     assert e.value.status == Bd.FW_ERR_INVALID_ARG
+    with pytest.raises(Bd.FwError) as e:
+        Bd.fw_seg_create(2, rp, col, w, 3, np.array([0, -1], np.int32),
+                         Bd.fw_seg_default_opts(index_width=16))
+    assert e.value.status == Bd.FW_ERR_INVALID_ARG
 
 
 def test_large_input_size_checks_before_upload(libpath):
