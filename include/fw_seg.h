@@ -326,9 +326,12 @@ void fw_batch_destroy(fw_batch *b);
  * device footprint fits in the free pool, uploaded and assembled on a side
  * stream while the current epoch runs, and joins the next epoch.  An epoch is
  * iters_per_epoch iterations of every resident request (four times as many
- * while no request waits for admission): one persistent launch over all of
- * them, or, when a single request is resident, the single-problem kernels of
- * fw_seg_solve for it.  Requests that meet their stop rule are harvested
+ * while no request waits for admission): the single-problem kernels of
+ * fw_seg_solve for one request -- the only resident one, or the oldest when it
+ * has at least 131,072 rows (enough to fill the GPU), first in, first out --
+ * or else one persistent launch over all of them.  Lone-request epochs run
+ * from a captured graph, two kept in flight ahead of the worker thread.
+ * Requests that meet their stop rule are harvested
  * (labels copied to the host) and their memory is reused.  Results are
  * bitwise the same as when the request is solved alone.
  * ---------------------------------------------------------------------- */

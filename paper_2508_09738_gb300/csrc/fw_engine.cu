@@ -144,6 +144,15 @@ public:
     // carry the 4-bit class array those kernels gather)
     bool plain_path = false;
     std::map<int, std::unique_ptr<Ops>> plain;   // per class bound
+    // Lone-problem epochs (serving): a captured graph of lone_iters fused
+    // iterations of slot lone_slot, kept up to two launches ahead of the host;
+    // after each launch the slot's state is copied into a pinned ring entry
+    // whose event the host waits for, so the GPU does not idle between epochs.
+    cudaGraphExec_t lone_graph = nullptr;
+    int lone_slot = -1, lone_iters = 0;
+    ProbState* h_ring = nullptr;                 // pinned [2]
+    cudaEvent_t ring_ev[2] = {nullptr, nullptr};
+    int ring_head = 0, ring_queued = 0;
     long long budget = 0;
     cudaGraphExec_t graph = nullptr;
     int graph_iters = -1;
@@ -155,6 +164,10 @@ public:
         if (stream) cudaStreamSynchronize(stream);
         if (side) cudaStreamSynchronize(side);
         if (graph) cudaGraphExecDestroy(graph);
+        if (lone_graph) cudaGraphExecDestroy(lone_graph);
+        for (cudaEvent_t ev : ring_ev)
+            if (ev) cudaEventDestroy(ev);
+        if (h_ring) cudaFreeHost(h_ring);
         for (void* p : {(void*)pool, (void*)d_desc, (void*)d_state, (void*)d_work, (void*)d_bar,
                         (void*)d_labels})
             if (p) cudaFree(p);
@@ -332,6 +345,12 @@ public:
     void remove(int s) {
         Slot& sl = slots[size_t(s)];
         if (!sl.used) return;
+        if (s == lone_slot) {   // queued lone epochs still name this slot's memory
+            drain_lone();
+            if (lone_graph) cudaGraphExecDestroy(lone_graph);
+            lone_graph = nullptr;
+            lone_slot = -1;
+        }
         ra.release(sl.off, sl.bytes);
         sl = Slot();
         work_dirty = true;
@@ -379,6 +398,7 @@ public:
     // Enqueue one persistent launch of `iters` iterations over the live
     // problems on `stream`; *nlive_out = live problems (0: nothing launched).
     fw_status launch(int iters, int* nlive_out) {
+        FW_TRY(drain_lone());
         const int nlive = build_work();
         *nlive_out = nlive;
         if (nlive == 0) return FW_OK;
@@ -441,6 +461,87 @@ public:
             it = plain.emplace(km, std::move(o)).first;
         }
         *out = it->second.get();
+        return FW_OK;
+    }
+
+    // The one live problem when there is exactly one (else -1).
+    int lone_live() const {
+        int live = -1, cnt = 0;
+        for (int s = 0; s < nslots(); ++s)
+            if (slots[size_t(s)].used && !h_state[s].done) {
+                live = s;
+                ++cnt;
+            }
+        return cnt == 1 ? live : -1;
+    }
+
+    // Wait for queued lone epochs; h_state then holds the device state.
+    fw_status drain_lone() {
+        if (ring_queued == 0) return FW_OK;
+        ring_queued = 0;
+        FW_CUDA(cudaStreamSynchronize(stream));
+        FW_CUDA(cudaMemcpy(h_state, d_state, sizeof(ProbState) * slots.size(),
+                           cudaMemcpyDeviceToHost));
+        return FW_OK;
+    }
+
+    // Queue lone epochs of `iters` iterations of slot s until two are in
+    // flight.  false: the stream cannot be captured (nothing queued).
+    fw_status lone_queue(int s, int iters, bool* ok) {
+        *ok = false;
+        if (!h_ring) {
+            FW_CUDA(cudaMallocHost(&h_ring, 2 * sizeof(ProbState)));
+            for (cudaEvent_t& ev : ring_ev)
+                FW_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        }
+        if (!lone_graph || lone_slot != s || lone_iters != iters) {
+            FW_TRY(drain_lone());
+            if (lone_graph) cudaGraphExecDestroy(lone_graph);
+            lone_graph = nullptr;
+            lone_slot = -1;
+            Ops* op = nullptr;
+            FW_TRY(plain_ops(slots[size_t(s)].lay.K, &op));
+            const ProbDesc& pd = slots[size_t(s)].pd;
+            ProbState* st = d_state + s;
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                for (int i = 0; i < iters; ++i) {
+                    op->passA(pd, st, stream, i > 0 ? 1 : 0);
+                    op->passB(pd, st, stream);
+                }
+                op->finish(pd, st, stream);
+                e = cudaStreamEndCapture(stream, &g);
+                if (e == cudaSuccess) e = cudaGraphInstantiate(&lone_graph, g, 0);
+                if (g) cudaGraphDestroy(g);
+            }
+            cudaGetLastError();
+            if (e != cudaSuccess) {
+                lone_graph = nullptr;
+                return FW_OK;
+            }
+            lone_slot = s;
+            lone_iters = iters;
+        }
+        while (ring_queued < 2) {
+            const int k = (ring_head + ring_queued) & 1;
+            FW_CUDA(cudaGraphLaunch(lone_graph, stream));
+            FW_CUDA(cudaMemcpyAsync(h_ring + k, d_state + s, sizeof(ProbState),
+                                    cudaMemcpyDeviceToHost, stream));
+            FW_CUDA(cudaEventRecord(ring_ev[k], stream));
+            ++ring_queued;
+        }
+        graph_captured = 1;
+        *ok = true;
+        return FW_OK;
+    }
+
+    // The state after the oldest queued lone epoch (the newer one keeps running).
+    fw_status lone_collect() {
+        FW_CUDA(cudaEventSynchronize(ring_ev[ring_head]));
+        h_state[lone_slot] = h_ring[ring_head];
+        ring_head ^= 1;
+        --ring_queued;
         return FW_OK;
     }
 
@@ -936,12 +1037,20 @@ void fw_batch_destroy(fw_batch* b) { delete b; }
 
 namespace {
 
+// A host array left uninitialised until filled (no zero-fill pass over
+// pages that the copy writes anyway).
+template <typename V>
+struct HostBuf {
+    std::unique_ptr<V[]> p;
+    V* data() { return p.get(); }
+};
+
 struct Request {
     uint64_t ticket = 0;
     int64_t n = 0;
     int32_t K = 0;
-    std::vector<int32_t> rp, col, labels;
-    std::vector<double> w;
+    HostBuf<int32_t> rp, col, labels;
+    HostBuf<double> w;
     fw_seg_opts opts{};
     ProbLayout lay;
     size_t bytes = 0;
@@ -955,6 +1064,42 @@ struct Result {
 };
 
 }  // namespace
+
+// memcpy split over up to 8 host threads for large arrays (a 1024^2 image's
+// request is about 110 MB; one thread copies it in about 9 ms on Grace).
+// Parts whose thread cannot be started are copied by the calling thread.
+static void copy_parallel(void* dst, const void* src, size_t bytes) {
+    constexpr size_t kChunk = size_t(8) << 20;
+    const size_t hw = std::max(1u, std::thread::hardware_concurrency());
+    const size_t nt = std::min<size_t>({8, hw, bytes / kChunk});
+    auto part = [&](size_t t) {
+        const size_t a = bytes * t / nt, b = bytes * (t + 1) / nt;
+        std::memcpy(static_cast<char*>(dst) + a, static_cast<const char*>(src) + a, b - a);
+    };
+    if (nt < 2) {
+        if (bytes) std::memcpy(dst, src, bytes);
+        return;
+    }
+    std::vector<std::thread> th;
+    size_t t = 1;
+    try {
+        for (; t < nt; ++t) th.emplace_back(part, t);
+    } catch (const std::system_error&) {
+    }
+    for (size_t u = t; u < nt; ++u) part(u);
+    part(0);
+    for (auto& x : th) x.join();
+}
+
+template <typename V>
+static void assign_parallel(HostBuf<V>& v, const V* src, size_t n) {
+    v.p.reset(new V[n > 0 ? n : 1]);
+    copy_parallel(v.data(), src, n * sizeof(V));
+}
+
+// A resident request with at least this many rows (about 512 row tiles of 256,
+// enough to fill a GB300 by itself) runs alone when it is the oldest.
+constexpr int64_t kAloneRows = int64_t(1) << 17;
 
 struct fw_srv {
     Engine eng;
@@ -1020,7 +1165,25 @@ void fw_srv::loop() {
             waiting = !queue.empty();
         }
         int nlive = 0;
-        fw_status rc = e.launch_epoch(so.iters_per_epoch * (waiting ? 1 : 4), &nlive);
+        const int iters = so.iters_per_epoch * (waiting ? 1 : 4);
+        // a lone resident, or the oldest resident when it is large enough to
+        // fill the GPU by itself, runs alone on the single-problem kernels
+        // (first in, first out); otherwise one persistent launch iterates all
+        int lone = e.lone_live();
+        if (lone < 0) {
+            uint64_t first = UINT64_MAX;
+            int oldest = -1;
+            for (int q = 0; q < e.nslots(); ++q)
+                if (e.slots[size_t(q)].used && !e.h_state[q].done && slot_ticket[size_t(q)] < first) {
+                    first = slot_ticket[size_t(q)];
+                    oldest = q;
+                }
+            if (oldest >= 0 && e.slots[size_t(oldest)].lay.n >= kAloneRows) lone = oldest;
+        }
+        bool piped = false;
+        fw_status rc = lone >= 0 ? e.lone_queue(lone, iters, &piped) : FW_OK;
+        if (rc == FW_OK && piped) nlive = 1;
+        else if (rc == FW_OK) rc = e.launch_epoch(iters, &nlive);
         // ... and admit queued requests (FIFO) while it runs: upload and
         // assembly go to the side stream, the pool range is taken in order
         for (;;) {
@@ -1054,7 +1217,7 @@ void fw_srv::loop() {
             }
         }
         if (rc == FW_OK && nlive > 0) {
-            rc = e.collect();
+            rc = piped ? e.lone_collect() : e.collect();
             std::lock_guard<std::mutex> lk(mu);
             info.epochs++;
             for (int s = 0; s < e.nslots(); ++s)
@@ -1160,10 +1323,10 @@ fw_status fw_srv_submit(fw_srv* s, const fw_graph* g, const fw_seg_opts* opts, u
         rq->K = g->K;
         rq->opts = o;
         const int64_t nnz = g->row_ptr_host[g->n];
-        rq->rp.assign(g->row_ptr_host, g->row_ptr_host + g->n + 1);
-        rq->col.assign(g->col_host, g->col_host + nnz);
-        rq->w.assign(g->w_host, g->w_host + nnz);
-        rq->labels.assign(g->labels_host, g->labels_host + g->n);
+        assign_parallel(rq->rp, g->row_ptr_host, size_t(g->n) + 1);
+        assign_parallel(rq->col, g->col_host, size_t(nnz));
+        assign_parallel(rq->w, g->w_host, size_t(nnz));
+        assign_parallel(rq->labels, g->labels_host, size_t(g->n));
         std::lock_guard<std::mutex> lk(s->mu);
         rq->ticket = s->next_ticket++;
         *ticket = rq->ticket;

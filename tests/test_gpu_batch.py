@@ -280,3 +280,26 @@ def test_server_lone_requests_and_wait_any():
         assert srv.wait_any(10) == (B.FW_PENDING, None)
         info = srv.info()
     assert info.completed == len(reqs) and info.failed == 0
+
+
+def test_server_large_oldest_runs_alone_equal_results():
+    """The oldest resident request runs alone when it has at least 2^17 rows;
+    small requests behind it share persistent launches once it is done.
+    Every result equals the request solved alone, bit for bit."""
+    reqs = [(W.voronoi_image(side=400, K=4, seed=71, label_frac=0.005),
+             dict(max_iters=120, omega0=1e5)),
+            (W.blobs_knn(n=900, K=3, seed=72), dict(max_iters=90)),
+            (W.voronoi_image(side=384, K=5, seed=73, label_frac=0.005),
+             dict(max_iters=100, gap_tol=1e-3, tol_mode="rel", omega0=1e5)),
+            (W.blobs_knn(n=1500, K=6, seed=74), dict(max_iters=150)),
+            (W.voronoi_image(side=50, K=3, seed=75, label_frac=0.02), dict(max_iters=70))]
+    assert reqs[0][0].n >= 1 << 17 and reqs[2][0].n >= 1 << 17
+    alone = [solve_alone(g, "f32", **o) for g, o in reqs]
+    with B.Server(hbm_budget_bytes=2 << 30, max_slots=8, max_K=8, iters_per_epoch=8) as srv:
+        tickets = [srv.submit(g, **o) for g, o in reqs]
+        for (g, o), t, (U, lab, st) in zip(reqs, tickets, alone):
+            rc, lab_s, st_s = srv.wait(t, g.n, timeout_ms=120_000)
+            assert rc == st.status and np.array_equal(lab_s, lab)
+            assert st_s.iters == st.iters and st_s.gap == st.gap and st_s.objective == st.objective
+        info = srv.info()
+    assert info.completed == len(reqs) and info.failed == 0
