@@ -127,6 +127,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 5 : 2) k_persistent(B
                                         bars, mb_phases);
                     else
                         tile_B<T, WT, KMAX, false, true>(s_pd[c], st, wk.y, sm_lane, sm_row,
+                                                         sm_row + kBlock * (KMAX | 1),
                                                          s_pd[c].acc, &a.bar->ndone);
                 }
                 __syncthreads();   // the prefetched slot is complete, the current one free
@@ -156,7 +157,8 @@ template <typename T, typename WT, int KMAX>
 class BatchKernImpl final : public BatchKern {
 public:
     size_t smem() const override {
-        const size_t b = 2 * size_t(kBlock) * (KMAX | 1) * sizeof(T);
+        const size_t b = 2 * size_t(kBlock) * (KMAX | 1) * sizeof(T) +
+                         passB_prefetch_bytes<T, KMAX>();
         const size_t a = 3 * size_t(kBlock) * KMAX * sizeof(T);   // one staging buffer
         const size_t r = size_t(kBlock) * kNumR * sizeof(double);
         const size_t m = a > b ? a : b;

@@ -179,6 +179,20 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     return mbar_test(bar, parity);
 }
 
+// 16-byte asynchronous global -> shared copies (L2 only, so data written by
+// other blocks before a grid barrier is seen), completed per thread.
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem_dst)),
+                 "l"(gmem_src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 // ------------------------------------------------------- block reductions
 // GB300 executes FP64 at a small fraction of the FP32 rate, so FP64 is used
 // only where sums span many tiles: rows of one 256-row tile are summed in the
@@ -1018,23 +1032,61 @@ __device__ __forceinline__ void csr_bins(const ProbDesc& pd, const T* __restrict
     }
 }
 
+// Shared memory pass B needs beyond its bins (sm_lane, sm_row): the rows' U
+// values and choice bytes, prefetched while the CSR rows are walked.
+template <typename T, int KMAX>
+__host__ __device__ constexpr size_t passB_prefetch_bytes() {
+    return size_t(kBlock) * KMAX * sizeof(T) + kBlock;
+}
+// Forms that prefetch: one lane per row with at most 8 classes (pixel grids
+// and other low-degree graphs, whose U streams from HBM; the extra shared
+// memory leaves their occupancy unchanged), and the persistent kernel (!RO).
+// The 2- and 4-lane forms for more classes keep their bins-only footprint,
+// which their one-wave occupancy and L1 class gathers need.
+template <int KMAX, bool RO, int LC>
+__host__ __device__ constexpr bool passB_prefetches() {
+    return (LC == 1 && KMAX <= 8) || !RO;
+}
+
 // Pass B over rows [r_begin, r_end): LS = L S (one-hot S) and sum_i <D_i, LS_i>.
+// sm_pf: passB_prefetch_bytes() of shared memory, 16-byte aligned.  Each warp
+// copies its 32 rows' U values (class-major, 128 bytes per class) and choice
+// bytes into it with asynchronous 16-byte copies before it walks their CSR
+// rows, so those loads do not add a memory latency after the walk.
 template <typename T, typename WT, int KMAX, bool RO, int LC = 0, bool EXACT = false>
 __device__ __forceinline__ void passB_rows(const ProbDesc& pd, int r_begin, int r_end, T& accq,
-                                           T* sm_lane, T* sm_row_in) {
+                                           T* sm_lane, T* sm_row_in, T* sm_pf) {
     constexpr int KP = KMAX | 1;
+    constexpr int kV = 16 / int(sizeof(T));   // values per 16-byte copy
+    constexpr int kC = 32 / kV;               // copies per class for a warp's 32 rows
     const int K = EXACT ? KMAX : pd.K;
     T* const sm_row = LC == 1 ? sm_lane : sm_row_in;   // one lane: its bins are the row sums
     const int64_t np = pd.npad;
     const T* __restrict__ Ub = static_cast<const T*>(pd.U);
     T* __restrict__ LSb = static_cast<T*>(pd.LS);
     const T* __restrict__ diag = static_cast<const T*>(pd.diag);
+    constexpr bool PF = passB_prefetches<KMAX, RO, LC>();
+    T* const sU = sm_pf;
+    uint8_t* const sC = reinterpret_cast<uint8_t*>(sm_pf + KMAX * kBlock);
+    const int lane = threadIdx.x & 31, w0 = threadIdx.x & ~31;
     for (int base = r_begin; base < r_end; base += kBlock) {
+        const int bw = base + w0;   // the warp's first row; U and choice are padded to 32 rows
+        if (PF && bw < r_end) {
+            for (int c = lane; c < K * kC; c += 32) {
+                const int k = c / kC, q = c - k * kC;
+                cp_async16(sU + k * kBlock + w0 + q * kV, Ub + k * np + bw + q * kV);
+            }
+            if (lane < 2) cp_async16(sC + w0 + 16 * lane, pd.choice + bw + 16 * lane);
+        }
+        if (PF) cp_async_commit();
         csr_bins<T, WT, KMAX, kSrcOneHot, RO, LC, EXACT>(pd, nullptr, base, r_end, sm_lane, sm_row);
-        // sm_row[t] was written by this thread's own warp
+        if (PF) {
+            cp_async_wait_all();
+            __syncwarp();   // the warp's copies (and its sm_row sums) are visible to all its lanes
+        }
         const int r = base + threadIdx.x;
         if (r < r_end) {
-            const uint8_t sv = ld_cg(pd.choice + r);
+            const uint8_t sv = PF ? sC[threadIdx.x] : ld_cg(pd.choice + r);
             const int si = sv & 0x7f;
             const bool act = (sv & kActiveBit) != 0;
             const T dg = pd.comb ? diag[r] : T(1);
@@ -1050,7 +1102,7 @@ __device__ __forceinline__ void passB_rows(const ProbDesc& pd, int r_begin, int 
                 T u[KMAX];
 #pragma unroll
                 for (int k = 0; k < KMAX; ++k)
-                    if (k < K) u[k] = ld_cg(Ub + k * np + r);
+                    if (k < K) u[k] = PF ? sU[k * kBlock + threadIdx.x] : ld_cg(Ub + k * np + r);
                 T qi = T(0);
 #pragma unroll
                 for (int k = 0; k < KMAX; ++k)
@@ -1171,11 +1223,12 @@ __device__ __forceinline__ void tile_A(const ProbDesc& pd, ProbState* st, int ti
 template <typename T, typename WT, int KMAX, bool RO, bool LAST, int LC = 0,
           bool EXACT = false>
 __device__ __forceinline__ void tile_B(const ProbDesc& pd, ProbState* st, int tile, T* sm_lane,
-                                       T* sm_row, unsigned long long* accb, uint32_t* ndone) {
+                                       T* sm_row, T* sm_pf, unsigned long long* accb,
+                                       uint32_t* ndone) {
     const int r0 = tile * pd.tile_rows;
     const int r1 = min(pd.n, r0 + pd.tile_rows);
     T accq = T(0);
-    passB_rows<T, WT, KMAX, RO, LC, EXACT>(pd, r0, r1, accq, sm_lane, sm_row);
+    passB_rows<T, WT, KMAX, RO, LC, EXACT>(pd, r0, r1, accq, sm_lane, sm_row, sm_pf);
     const T v[kNumB] = {accq};
     block_accumulate<T, kNumB>(v, accb, kNumA, tile % kAccCopies);
     if (LAST && last_to_arrive(&st->cnt, pd.ntiles) && threadIdx.x < 32) {

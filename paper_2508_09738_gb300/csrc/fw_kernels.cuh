@@ -119,7 +119,8 @@ __global__ void __launch_bounds__(kBlock) k_passB(ProbDesc pd, ProbState* st) {
     extern __shared__ __align__(128) unsigned char smraw[];
     T* sm_lane = reinterpret_cast<T*>(smraw);
     T* sm_row = sm_lane + kBlock * (KMAX | 1);
-    tile_B<T, WT, KMAX, true, false>(pd, st, blockIdx.x, sm_lane, sm_row, accb, nullptr);
+    tile_B<T, WT, KMAX, true, false>(pd, st, blockIdx.x, sm_lane, sm_row,
+                                     sm_row + kBlock * (KMAX | 1), accb, nullptr);
 }
 
 // Pass B with LC lanes per row known at compile time (1 for low-degree graphs
@@ -133,8 +134,8 @@ __device__ __forceinline__ void passB_lc_body(const ProbDesc& pd, ProbState* st)
     extern __shared__ __align__(128) unsigned char smraw[];
     T* sm_lane = reinterpret_cast<T*>(smraw);
     T* sm_row = sm_lane + kBlock * (KMAX | 1);
-    tile_B<T, WT, KMAX, true, false, LC, EXACT>(pd, st, blockIdx.x, sm_lane, sm_row, accb,
-                                                nullptr);
+    tile_B<T, WT, KMAX, true, false, LC, EXACT>(pd, st, blockIdx.x, sm_lane, sm_row,
+                                                sm_row + kBlock * (KMAX | 1), accb, nullptr);
 }
 
 template <typename T, typename WT, int KMAX, int LC, bool EXACT>

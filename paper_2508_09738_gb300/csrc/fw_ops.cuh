@@ -20,6 +20,13 @@ public:
     int kmax() const override { return KMAX; }
     // pass B / SpMM bins
     static size_t smem() { return 2 * size_t(kBlock) * (KMAX | 1) * sizeof(T); }
+    // pass B: bins plus, in the forms that prefetch, the rows' U values and
+    // choice bytes
+    static size_t smemB() { return smem() + passB_prefetch_bytes<T, KMAX>(); }
+    template <int LC>
+    static size_t smemB_lc() {
+        return passB_prefetches<KMAX, true, LC>() ? smemB() : smem();
+    }
     static size_t smemA() { return max_stages<T, KMAX>() * 3 * size_t(kBlock) * KMAX * sizeof(T); }
     static size_t smemA(const ProbDesc& pd) {
         return (pd.tile_rows > kBlock ? max_stages<T, KMAX>() : 1) * 3 * size_t(kBlock) * KMAX *
@@ -38,7 +45,7 @@ public:
             if (e != cudaSuccess) return e;
         }
         e = cudaFuncSetAttribute(k_passB<T, WT, KMAX>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem()));
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, int(smemB()));
         if (e != cudaSuccess) return e;
         e = cudaFuncSetAttribute(k_osfw<T, WT, KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  int(smem()));
@@ -46,7 +53,7 @@ public:
         for (auto f : {k_passB_lc<T, WT, KMAX, 1, false>, k_passB_lc<T, WT, KMAX, 2, false>,
                        k_passB_lc<T, WT, KMAX, 4, false>, k_passB_lc6<T, WT, KMAX, 2, false>,
                        k_passB_lc6<T, WT, KMAX, 4, false>}) {
-            e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem()));
+            e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smemB()));
             if (e != cudaSuccess) return e;
         }
         if constexpr (kExactB) {
@@ -54,7 +61,7 @@ public:
                            k_passB_lc<T, WT, KMAX, 4, true>, k_passB_lc6<T, WT, KMAX, 2, true>,
                            k_passB_lc6<T, WT, KMAX, 4, true>}) {
                 e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         int(smem()));
+                                         int(smemB()));
                 if (e != cudaSuccess) return e;
             }
         }
@@ -85,19 +92,19 @@ public:
     void passB_lanes(const ProbDesc& pd, ProbState* st, cudaStream_t s) {
         const unsigned g = unsigned(pd.ntiles);
         if (pd.lanes == 1)
-            k_passB_lc<T, WT, KMAX, 1, EXACT><<<g, kBlock, smem(), s>>>(pd, st);
+            k_passB_lc<T, WT, KMAX, 1, EXACT><<<g, kBlock, smemB_lc<1>(), s>>>(pd, st);
         else if (pd.lanes == 2 && kBound6)
-            k_passB_lc6<T, WT, KMAX, 2, EXACT><<<g, kBlock, smem(), s>>>(pd, st);
+            k_passB_lc6<T, WT, KMAX, 2, EXACT><<<g, kBlock, smemB_lc<2>(), s>>>(pd, st);
         else if (pd.lanes == 4 && kBound6)
-            k_passB_lc6<T, WT, KMAX, 4, EXACT><<<g, kBlock, smem(), s>>>(pd, st);
+            k_passB_lc6<T, WT, KMAX, 4, EXACT><<<g, kBlock, smemB_lc<4>(), s>>>(pd, st);
         else if (pd.lanes == 2)
-            k_passB_lc<T, WT, KMAX, 2, EXACT><<<g, kBlock, smem(), s>>>(pd, st);
+            k_passB_lc<T, WT, KMAX, 2, EXACT><<<g, kBlock, smemB_lc<2>(), s>>>(pd, st);
         else
-            k_passB_lc<T, WT, KMAX, 4, EXACT><<<g, kBlock, smem(), s>>>(pd, st);
+            k_passB_lc<T, WT, KMAX, 4, EXACT><<<g, kBlock, smemB_lc<4>(), s>>>(pd, st);
     }
     void passB(const ProbDesc& pd, ProbState* st, cudaStream_t s) override {
         if (pd.lanes != 1 && pd.lanes != 2 && pd.lanes != 4) {
-            k_passB<T, WT, KMAX><<<unsigned(pd.ntiles), kBlock, smem(), s>>>(pd, st);
+            k_passB<T, WT, KMAX><<<unsigned(pd.ntiles), kBlock, smemB_lc<0>(), s>>>(pd, st);
             return;
         }
         if constexpr (kExactB) {
