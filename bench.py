@@ -55,6 +55,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-trajectory", action="store_true")
+    p.add_argument("--problems", type=int, default=256, help="batched: number of problems")
     return p.parse_args()
 
 
@@ -355,7 +356,7 @@ def run_batched(args, rank, world, local):
     from paper_2508_09738_gb300 import build as Bld
     torch.cuda.set_device(local)
     Bld.build()
-    P = 256
+    P = args.problems
     t0 = time.time()
     gs = W.batched_blobs(P=P, n_min=1000, n_max=200_000, K_min=3, K_max=10, label_frac=0.02,
                          seed=W.SEED0 + 3, device="cuda")
@@ -437,7 +438,7 @@ def run_batched(args, rank, world, local):
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000 * t_b / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "batched256", "problems": P, "rows": sum(g.n for g in gs),
+        "config": {"workload": "batched256" if P == 256 else f"batched{P}", "problems": P, "rows": sum(g.n for g in gs),
                    "nnz": sum(g.nnz for g in gs), "K": "3..10", "iters_per_solve": iters,
                    "weights": weights, "eps": 50.0, "omega0": 1000.0,
                    "l2": "256 MiB buffer written between timed steps"},
