@@ -56,6 +56,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-trajectory", action="store_true")
     p.add_argument("--problems", type=int, default=256, help="batched: number of problems")
+    p.add_argument("--no-extras", action="store_true",
+                   help="single-problem workloads: skip the batched and serving sub-records")
     return p.parse_args()
 
 
@@ -349,8 +351,9 @@ def whole_job_rate(units_per_rank: float, seconds_local: float, world: int, devi
 
 
 # --------------------------------------------------------------- batched --
-def run_batched(args, rank, world, local):
-    """256 uneven blob problems in one persistent launch vs 256 sequential solves."""
+def run_batched(args, rank, world, local, emit=True):
+    """256 uneven blob problems in one persistent launch vs 256 sequential
+    solves; prints the JSON line (emit) and returns it."""
     import torch
     from paper_2508_09738_gb300 import binding as B
     from paper_2508_09738_gb300 import build as Bld
@@ -456,13 +459,15 @@ def run_batched(args, rank, world, local):
         "setup_s": {"generate": gen_s, "create_and_tune": create_s},
     }
     bt.close()
-    if rank == 0:
+    if rank == 0 and emit:
         print(json.dumps(line), flush=True)
+    return line
 
 
 # --------------------------------------------------------------- serving --
-def run_serving(args, rank, world, local):
-    """Poisson requests at swept rates: continuous batching vs sequential solves."""
+def run_serving(args, rank, world, local, emit=True):
+    """Poisson requests at swept rates: continuous batching vs sequential
+    solves; prints the JSON line (emit) and returns it."""
     import torch
     from paper_2508_09738_gb300 import binding as B
     from paper_2508_09738_gb300 import build as Bld
@@ -561,8 +566,9 @@ def run_serving(args, rank, world, local):
         "sequential_capacity_per_s": cap, "rates": rates, "server": info,
         "setup_s": {"generate": gen_s},
     }
-    if rank == 0:
+    if rank == 0 and emit:
         print(json.dumps(line), flush=True)
+    return line
 
 
 # ------------------------------------------------------------------ ours --
@@ -935,9 +941,24 @@ def run_single(args, rank, world, local):
         line[w] = recs[w]
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(g, c, arms[0], args.cpu_seconds)
+    if not args.no_extras and world == 1:
+        line.update(extras(args, rank, world, local))
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def extras(args, rank, world, local):
+    """Compact runs of the batched (256 problems, 2 timed steps) and serving
+    (100 Poisson requests per rate) workloads, as sub-records of the line."""
+    import copy
+    a = copy.copy(args)
+    a.steps, a.warmup, a.iters, a.weights, a.lanes, a.problems = 2, 1, 0, "", 0, 256
+    out = {"batched256": run_batched(a, rank, world, local, emit=False)}
+    s = copy.copy(args)
+    s.steps = 5
+    out["serving"] = run_serving(s, rank, world, local, emit=False)
+    return out
 
 
 def main():
