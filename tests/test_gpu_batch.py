@@ -35,7 +35,7 @@ def solve_alone(g, weights, **opts):
 
 @pytest.mark.parametrize("weights", ["f32", "bf16"])
 @pytest.mark.parametrize("schedule,bps,lanes", [("static", 1, 0), ("dynamic", 2, 4),
-                                                ("static", 0, -1)])
+                                                ("dynamic", 2, 2), ("static", 0, -1)])
 def test_batch_bitwise_equals_single(weights, schedule, bps, lanes):
     """Batched solves equal single solves bit for bit when both use the same
     lanes per row (the batch's tuned or fixed count, reported by info())."""
@@ -303,3 +303,23 @@ def test_server_large_oldest_runs_alone_equal_results():
             assert st_s.iters == st.iters and st_s.gap == st.gap and st_s.objective == st.objective
         info = srv.info()
     assert info.completed == len(reqs) and info.failed == 0
+
+
+@pytest.mark.parametrize("weights", ["f32", "bf16", "f64"])
+def test_two_lane_pass_b_bitwise_equals_persistent(weights):
+    """With two lanes per row the single-problem pass B lets each row's two
+    lanes finish it (half the classes each, the <D, L S> chain handed from
+    one lane to the other); the persistent kernel sums the lanes first and
+    finishes the row in one thread.  Same operations in the same order: the
+    iterates must agree bit for bit, for exact and guarded class counts."""
+    gs = [W.sbm(n=307 * K, K=K, deg_in=20.0, deg_out=2.0, label_frac=0.02, seed=90 + K)
+          for K in (3, 4, 7, 10, 12, 13)]
+    iters = 25
+    opts = B.fw_seg_default_opts(max_iters=iters, weight_dtype=weights, lanes_per_row=2)
+    with B.Batch(gs, opts, weight_dtype=weights, lanes_per_row=2, blocks_per_sm=2,
+                 schedule="static", iters_per_launch=0) as b:
+        stats = b.solve()
+        for p, g in enumerate(gs):
+            U, lab, st = solve_alone(g, weights, max_iters=iters, lanes_per_row=2)
+            assert np.array_equal(b.U(p), U), (p, g.K)
+            assert stats[p].gap == st.gap and stats[p].objective == st.objective, (p, g.K)
