@@ -307,11 +307,11 @@ def test_server_large_oldest_runs_alone_equal_results():
 
 @pytest.mark.parametrize("weights", ["f32", "bf16", "f64"])
 def test_two_lane_pass_b_bitwise_equals_persistent(weights):
-    """With two lanes per row the single-problem pass B lets each row's two
-    lanes finish it (half the classes each, the <D, L S> chain handed from
-    one lane to the other); the persistent kernel sums the lanes first and
-    finishes the row in one thread.  Same operations in the same order: the
-    iterates must agree bit for bit, for exact and guarded class counts."""
+    """Two lanes per CSR row: the single-problem pass B (compile-time lane
+    count, exact-class and 40-register forms) and the persistent kernel
+    (runtime lane count) add each row's entries and lanes in the same order,
+    so the iterates agree bit for bit, for exact and guarded class counts
+    and every weight type."""
     gs = [W.sbm(n=307 * K, K=K, deg_in=20.0, deg_out=2.0, label_frac=0.02, seed=90 + K)
           for K in (3, 4, 7, 10, 12, 13)]
     iters = 25
