@@ -244,7 +244,11 @@ typedef struct fw_graph {
     const int32_t *labels_host;
 } fw_graph;
 
-enum { FW_SCHED_AUTO = 0, FW_SCHED_STATIC = 1, FW_SCHED_DYNAMIC = 2 };
+/* Schedules of a batch: the persistent cooperative kernel with a static grid
+ * stride or an atomic work counter over the (problem, tile) items, or
+ * per-item launches (each iteration one launch of the single-problem pass A
+ * over all items and one of pass B, kernel boundaries as the barriers). */
+enum { FW_SCHED_AUTO = 0, FW_SCHED_STATIC = 1, FW_SCHED_DYNAMIC = 2, FW_SCHED_ITEMS = 3 };
 /* How a persistent launch is issued: directly; from a captured CUDA graph,
  * with a failed capture an error (FW_ERR_CUDA); or from a captured graph when
  * the stream can be captured, else directly (fw_batch_info says which). */
@@ -253,8 +257,7 @@ enum { FW_GRAPH_OFF = 0, FW_GRAPH_REQUIRED = 1, FW_GRAPH_PREFERRED = 2 };
 typedef struct fw_batch_opts {
     int32_t weight_dtype;      /* FW_WEIGHTS_*, shared by every problem */
     int32_t blocks_per_sm;     /* 0: autotune (cached) */
-    int32_t schedule;          /* FW_SCHED_*: static grid stride or atomic work counter
-                                  (AUTO: autotuned) */
+    int32_t schedule;          /* FW_SCHED_* (AUTO: autotuned) */
     int32_t iters_per_launch;  /* -1: autotune; 0: every iteration in one launch */
     int32_t use_graph;         /* FW_GRAPH_* (default FW_GRAPH_REQUIRED) */
     int32_t spin_budget_ms;    /* bound on one grid-barrier wait */
@@ -270,7 +273,7 @@ typedef struct fw_batch_opts {
 typedef struct fw_batch_info {
     int32_t grid;              /* blocks of the persistent launch */
     int32_t blocks_per_sm;
-    int32_t schedule;          /* FW_SCHED_STATIC or FW_SCHED_DYNAMIC */
+    int32_t schedule;          /* FW_SCHED_STATIC, FW_SCHED_DYNAMIC or FW_SCHED_ITEMS */
     int32_t graph_captured;    /* 1 if the last launch ran from a captured CUDA graph */
     int32_t tuned;             /* 0 set by the caller, 1 measured now, 2 from the cache */
     int32_t kmax;              /* class bound of the persistent kernel (>= the largest K) */
@@ -290,7 +293,8 @@ typedef struct fw_batch fw_batch;
  *
  * Autotuning (at create, when any of those four is left to it) times a few
  * iterations of the batch itself, from U_0, for each candidate, one
- * dimension after the other: blocks per SM x schedule; then lanes per CSR
+ * dimension after the other: the schedule (per-item launches, or the
+ * persistent kernel static or dynamic at each blocks-per-SM count); then lanes per CSR
  * row (each problem's own count, or 1, 2, 4, 8 for all); then the class
  * bound the persistent kernel is compiled for (the smallest one that holds
  * the batch's largest K, or the next); then iterations per launch (all, 64

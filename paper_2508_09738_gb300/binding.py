@@ -93,7 +93,7 @@ class fw_srv_info(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
-SCHED = {"auto": 0, "static": 1, "dynamic": 2}
+SCHED = {"auto": 0, "static": 1, "dynamic": 2, "items": 3}
 GRAPH = {"off": 0, "required": 1, "preferred": 2}
 
 _lib = None

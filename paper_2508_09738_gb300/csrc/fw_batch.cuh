@@ -7,7 +7,7 @@
 // rule as the single-problem kernels, so a problem's arithmetic does not
 // depend on the batch it runs in.
 #pragma once
-#include "fw_device.cuh"
+#include "fw_kernels.cuh"
 
 namespace fw {
 
@@ -143,7 +143,67 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 5 : 2) k_persistent(B
     }
 }
 
-// Launcher of the persistent kernel for one (T, WT, KMAX).
+// ---------------------------------------------------- per-item schedule
+// The alternative to the persistent kernel: per iteration one launch of the
+// single-problem pass A over every (problem, tile) item of the live
+// problems, one launch of pass B, and after the last iteration one warp per
+// live problem to finish, all captured in a CUDA graph; the kernel
+// boundaries are the grid-wide barriers.  Each block copies its item's
+// descriptor into shared memory and runs the single-problem per-tile code,
+// so every problem's arithmetic is that of solving it alone (with the same
+// lanes per row), and tens of thousands of item blocks keep the SMs busy.
+struct ItemArgs {
+    const ProbDesc* desc;   // [slots]
+    ProbState* state;       // [slots]
+    const int2* work;       // [nwork] (problem, tile) of the live problems
+    const int* live;        // [nlive] live problems
+};
+
+// Warp 0 copies the item's descriptor (8-byte words) into shared memory.
+__device__ __forceinline__ int2 item_desc(const ItemArgs& a, ProbDesc* s_pd) {
+    static_assert(sizeof(ProbDesc) % 8 == 0 && sizeof(ProbDesc) / 8 <= 32, "descriptor words");
+    const int2 wk = a.work[blockIdx.x];
+    if (threadIdx.x < sizeof(ProbDesc) / 8)
+        reinterpret_cast<unsigned long long*>(s_pd)[threadIdx.x] =
+            reinterpret_cast<const unsigned long long*>(a.desc + wk.x)[threadIdx.x];
+    __syncthreads();
+    return wk;
+}
+
+template <typename T, int KMAX>
+__global__ void __launch_bounds__(kBlock, passA_min_blocks<T, KMAX>()) k_itemA(ItemArgs a, int fin) {
+    __shared__ __align__(16) ProbDesc s_pd;
+    const int2 wk = item_desc(a, &s_pd);
+    extern __shared__ __align__(128) unsigned char smraw[];
+    passA_step<T, KMAX, false>(s_pd, a.state + wk.x, fin, reinterpret_cast<T*>(smraw), wk.y);
+}
+
+template <typename T, typename WT, int KMAX>
+__global__ void __launch_bounds__(kBlock) k_itemB(ItemArgs a) {
+    __shared__ __align__(16) ProbDesc s_pd;
+    const int2 wk = item_desc(a, &s_pd);
+    ProbState* st = a.state + wk.x;
+    bool done;
+    unsigned long long* accb = passB_bank(s_pd, st, done, wk.y);
+    if (done) return;
+    extern __shared__ __align__(128) unsigned char smraw[];
+    T* sm_lane = reinterpret_cast<T*>(smraw);
+    T* sm_row = sm_lane + kBlock * (KMAX | 1);
+    tile_B<T, WT, KMAX, true, false>(s_pd, st, wk.y, sm_lane, sm_row,
+                                     sm_row + kBlock * (KMAX | 1), accb, nullptr);
+}
+
+// One warp per live problem: the step decision of the last iteration.
+static __global__ void k_itemFinish(ItemArgs a) {
+    const int p = a.live[blockIdx.x];
+    ProbState* st = a.state + p;
+    if (ld_cg(&st->done)) return;
+    const ProbDesc& pd = a.desc[p];
+    warp_finish(pd, st, pd.acc + ld_cg(&st->cur) * kAccBank);
+}
+
+// Launcher of the persistent kernel (and of the per-item schedule) for one
+// (T, WT, KMAX).
 class BatchKern {
 public:
     virtual ~BatchKern() {}
@@ -151,6 +211,10 @@ public:
     virtual cudaError_t configure() = 0;
     virtual cudaError_t occupancy(int* blocks_per_sm) = 0;
     virtual cudaError_t launch(const BatchArgs& a, int grid, cudaStream_t s) = 0;
+    // `iters` iterations of the per-item schedule; two_stage: some live
+    // problem has tiles of more than one 256-row sub-tile
+    virtual cudaError_t launch_items(const ItemArgs& a, int nwork, int nlive, int iters,
+                                     bool two_stage, cudaStream_t s) = 0;
 };
 
 template <typename T, typename WT, int KMAX>
@@ -164,9 +228,32 @@ public:
         const size_t m = a > b ? a : b;
         return m > r ? m : r;
     }
+    static size_t smem_itemA(bool two_stage) {
+        return (two_stage ? max_stages<T, KMAX>() : 1) * 3 * size_t(kBlock) * KMAX * sizeof(T);
+    }
+    static size_t smem_itemB() {
+        return 2 * size_t(kBlock) * (KMAX | 1) * sizeof(T);
+    }
     cudaError_t configure() override {
-        return cudaFuncSetAttribute(k_persistent<T, WT, KMAX>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem()));
+        cudaError_t e = cudaFuncSetAttribute(k_persistent<T, WT, KMAX>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             int(smem()));
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(k_itemA<T, KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 int(smem_itemA(true)));
+        if (e != cudaSuccess) return e;
+        return cudaFuncSetAttribute(k_itemB<T, WT, KMAX>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    int(smem_itemB()));
+    }
+    cudaError_t launch_items(const ItemArgs& a, int nwork, int nlive, int iters, bool two_stage,
+                             cudaStream_t s) override {
+        for (int i = 0; i < iters; ++i) {
+            k_itemA<T, KMAX><<<nwork, kBlock, smem_itemA(two_stage), s>>>(a, i > 0 ? 1 : 0);
+            k_itemB<T, WT, KMAX><<<nwork, kBlock, smem_itemB(), s>>>(a);
+        }
+        k_itemFinish<<<nlive, 32, 0, s>>>(a);
+        return cudaGetLastError();
     }
     cudaError_t occupancy(int* bps) override {
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_persistent<T, WT, KMAX>, kBlock,

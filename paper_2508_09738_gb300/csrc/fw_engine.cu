@@ -131,6 +131,9 @@ public:
     int2* d_work = nullptr;
     size_t work_cap = 0;
     std::vector<int2> h_work;
+    int* d_live = nullptr;          // live problems (per-item schedule's finish)
+    std::vector<int> h_live;
+    bool two_stage = false;         // a live problem has multi-sub-tile tiles
     GridBar* d_bar = nullptr;
     GridBar* h_bar = nullptr;      // pinned
     int sms = 0, occ = 0, bps = 0, grid = 0, schedule = FW_SCHED_DYNAMIC;
@@ -169,7 +172,7 @@ public:
             if (ev) cudaEventDestroy(ev);
         if (h_ring) cudaFreeHost(h_ring);
         for (void* p : {(void*)pool, (void*)d_desc, (void*)d_state, (void*)d_work, (void*)d_bar,
-                        (void*)d_labels})
+                        (void*)d_labels, (void*)d_live})
             if (p) cudaFree(p);
         if (h_state) cudaFreeHost(h_state);
         if (h_bar) cudaFreeHost(h_bar);
@@ -211,6 +214,7 @@ public:
         slots.assign(size_t(max_slots), Slot());
         FW_TRY(dev_alloc((void**)&d_desc, sizeof(ProbDesc) * size_t(max_slots)));
         FW_TRY(dev_alloc((void**)&d_state, sizeof(ProbState) * size_t(max_slots)));
+        FW_TRY(dev_alloc((void**)&d_live, sizeof(int) * size_t(max_slots)));
         FW_CUDA(cudaMemset(d_state, 0, sizeof(ProbState) * size_t(max_slots)));
         FW_CUDA(cudaMallocHost(&h_state, sizeof(ProbState) * size_t(max_slots)));
         std::memset(h_state, 0, sizeof(ProbState) * size_t(max_slots));
@@ -236,7 +240,7 @@ public:
         if (clock_khz <= 0) clock_khz = 2100000;
         budget = (long long)std::max(spin_ms, 1) * (long long)clock_khz;
         set_grid(blocks_per_sm > 0 ? blocks_per_sm : occ,
-                 sched == FW_SCHED_STATIC ? FW_SCHED_STATIC : FW_SCHED_DYNAMIC);
+                 (sched == FW_SCHED_STATIC || sched == FW_SCHED_ITEMS) ? sched : FW_SCHED_DYNAMIC);
         return FW_OK;
     }
 
@@ -362,14 +366,23 @@ public:
 
     // Work list of the live problems (used and not done).
     int build_work() {
-        h_work.clear();
-        int nlive = 0;
+        std::vector<int2> w;
+        std::vector<int> live;
+        bool two = false;
         for (int s = 0; s < nslots(); ++s) {
             if (!slots[size_t(s)].used || h_state[s].done) continue;
-            ++nlive;
-            for (int t = 0; t < slots[size_t(s)].lay.ntiles; ++t) h_work.push_back(make_int2(s, t));
+            live.push_back(s);
+            two = two || slots[size_t(s)].lay.tile_rows > kBlock;
+            for (int t = 0; t < slots[size_t(s)].lay.ntiles; ++t) w.push_back(make_int2(s, t));
         }
-        return nlive;
+        if (w.size() != h_work.size() || live != h_live ||
+            !std::equal(w.begin(), w.end(), h_work.begin(),
+                        [](const int2& x, const int2& y) { return x.x == y.x && x.y == y.y; }))
+            work_dirty = true;
+        h_work.swap(w);
+        h_live.swap(live);
+        two_stage = two;
+        return int(h_live.size());
     }
 
     fw_status ensure_work_cap(size_t n) {
@@ -406,10 +419,23 @@ public:
             FW_TRY(ensure_work_cap(h_work.size()));
             FW_CUDA(cudaMemcpyAsync(d_work, h_work.data(), sizeof(int2) * h_work.size(),
                                     cudaMemcpyHostToDevice, stream));
+            FW_CUDA(cudaMemcpyAsync(d_live, h_live.data(), sizeof(int) * h_live.size(),
+                                    cudaMemcpyHostToDevice, stream));
             invalidate_graph();
             work_dirty = false;
         }
         const BatchArgs a = args(nlive, iters);
+        const ItemArgs ia{d_desc, d_state, d_work, d_live};
+        const bool items = schedule == FW_SCHED_ITEMS;
+        // one launch's work: the barrier record cleared, then the persistent
+        // kernel or the per-item launches
+        auto enqueue = [&]() -> cudaError_t {
+            cudaError_t e = cudaMemsetAsync(d_bar, 0, sizeof(GridBar), stream);
+            if (e != cudaSuccess) return e;
+            if (items)
+                return bk->launch_items(ia, int(h_work.size()), nlive, iters, two_stage, stream);
+            return bk->launch(a, grid, stream);
+        };
         bool from_graph = false;
         if (use_graph != FW_GRAPH_OFF) {
             if (!graph || graph_iters != iters) {
@@ -417,10 +443,9 @@ public:
                 cudaGraph_t g = nullptr;
                 cudaError_t e = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal);
                 if (e == cudaSuccess) {
-                    const cudaError_t e1 = cudaMemsetAsync(d_bar, 0, sizeof(GridBar), stream);
-                    const cudaError_t e2 = bk->launch(a, grid, stream);
+                    const cudaError_t e2 = enqueue();
                     e = cudaStreamEndCapture(stream, &g);
-                    if (e == cudaSuccess) e = e1 != cudaSuccess ? e1 : e2;
+                    if (e == cudaSuccess) e = e2;
                     if (e == cudaSuccess) e = cudaGraphInstantiate(&graph, g, 0);
                     if (g) cudaGraphDestroy(g);
                 }
@@ -443,10 +468,7 @@ public:
                 from_graph = true;
             }
         }
-        if (!from_graph) {
-            FW_CUDA(cudaMemsetAsync(d_bar, 0, sizeof(GridBar), stream));
-            FW_CUDA(bk->launch(a, grid, stream));
-        }
+        if (!from_graph) FW_CUDA(enqueue());
         graph_captured = from_graph ? 1 : 0;
         return FW_OK;
     }
@@ -802,7 +824,8 @@ static fw_status batch_tune(fw_batch* b) {
     c.kmax = e.kmax;
     c.lanes = std::max(0, o.lanes_per_row);
     c.ipl = std::max(0, o.iters_per_launch);
-    c.sched = o.schedule == FW_SCHED_STATIC ? FW_SCHED_STATIC : FW_SCHED_DYNAMIC;
+    c.sched = (o.schedule == FW_SCHED_STATIC || o.schedule == FW_SCHED_ITEMS) ? o.schedule
+                                                                               : FW_SCHED_DYNAMIC;
     c.bps = o.blocks_per_sm > 0 ? std::min(o.blocks_per_sm, e.occ) : e.occ;
     const int it = 4;
     float best = 1e30f, ms = 0.f;
@@ -815,10 +838,12 @@ static fw_status batch_tune(fw_batch* b) {
         }
         return FW_OK;
     };
-    // blocks per SM x schedule
+    // schedule: per-item launches, or the persistent kernel (static or
+    // dynamic) at each blocks-per-SM count
     {
         std::vector<int> scheds;
-        if (o.schedule == FW_SCHED_AUTO) scheds = {FW_SCHED_STATIC, FW_SCHED_DYNAMIC};
+        if (o.schedule == FW_SCHED_AUTO)
+            scheds = {FW_SCHED_ITEMS, FW_SCHED_STATIC, FW_SCHED_DYNAMIC};
         else scheds = {c.sched};
         std::vector<int> grids;
         if (o.blocks_per_sm > 0) grids = {c.bps};
@@ -827,6 +852,7 @@ static fw_status batch_tune(fw_batch* b) {
         const TuneChoice base = c;
         for (int sc : scheds)
             for (int x : grids) {
+                if (sc == FW_SCHED_ITEMS && x != grids.back()) continue;   // one candidate
                 TuneChoice t = base;
                 t.sched = sc;
                 t.bps = x;
@@ -920,6 +946,7 @@ fw_status fw_batch_create(fw_batch** out, int32_t P, const fw_graph* graphs,
             const fw_graph& g = graphs[p];
             const HostGraph hg{g.n, g.row_ptr_host, g.col_host, g.w_host, g.K, g.labels_host};
             FW_TRY(plan_problem(hg, o, lays[size_t(p)]));
+            lays[size_t(p)].cls4 = g.K <= 16;   // gathered by the per-item schedule's pass B
             Kmax = std::max(Kmax, g.K);
             b->max_iters = std::max(b->max_iters, o.max_iters);
             const size_t te = b->bo.weight_dtype == FW_WEIGHTS_F64 ? 8 : 4;
@@ -1277,7 +1304,9 @@ fw_status fw_srv_create(fw_srv** out, const fw_srv_opts* opts) {
         s->eng.plain_path = true;
         FW_TRY(s->eng.init(o.weight_dtype, o.max_K, o.hbm_budget_bytes, o.max_slots, o.cuda_stream,
                            o.spin_budget_ms > 0 ? o.spin_budget_ms : 2000, o.blocks_per_sm,
-                           o.schedule == FW_SCHED_STATIC ? FW_SCHED_STATIC : FW_SCHED_DYNAMIC));
+                           (o.schedule == FW_SCHED_STATIC || o.schedule == FW_SCHED_ITEMS)
+                               ? o.schedule
+                               : FW_SCHED_DYNAMIC));
         s->slot_ticket.assign(size_t(o.max_slots), 0);
         s->slot_epochs.assign(size_t(o.max_slots), 0);
         s->info.pool_bytes = s->eng.ra.cap();

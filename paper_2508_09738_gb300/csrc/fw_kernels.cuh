@@ -8,21 +8,28 @@ namespace fw {
 // Step pass A of one tile (k_passA, k_passA_exact).  With `fin` the block first
 // takes the previous iteration's step decision itself (no k_finish between
 // the passes; see ProbState); otherwise it applies the step k_finish stored.
+// `tile`: the problem's row tile this block works on (its block index in the
+// single-problem launch, its work item's tile in a batched item launch).
 template <typename T, int KMAX, bool EXACT>
-__device__ __forceinline__ void passA_step(const ProbDesc& pd, ProbState* st, int fin, T* stage) {
+__device__ __forceinline__ void passA_step(const ProbDesc& pd, ProbState* st, int fin, T* stage,
+                                           int tile) {
     __shared__ __align__(8) uint64_t bars[2];
     __shared__ double s_alpha;
-    __shared__ int s_stop;
-    const int done = ld_cg(&st->done);
+    __shared__ int s_stop, s_done;
+    // Block 0 of this launch may commit a stop (done = 1) while other blocks
+    // start: one thread reads the flag and the whole block follows it, so no
+    // block splits between leaving and waiting on the bulk copies.
+    if (threadIdx.x == 0) s_done = ld_cg(&st->done);
+    __syncthreads();
+    if (s_done) return;
     const int c = ld_cg(&st->cur);
-    if (done) return;
     if (threadIdx.x == 0) {
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
         if (fin) {   // the first copies go out at once (a step is always pending)
-            const int r0 = blockIdx.x * pd.tile_rows;
+            const int r0 = tile * pd.tile_rows;
             stage_issue<T, KMAX>(pd, r0, min(kBlock, pd.n - r0), true, stage, &bars[0]);
-        } else if (blockIdx.x == 0) {
+        } else if (tile == 0) {
             st->cur_b = c;
         }
     }
@@ -30,11 +37,11 @@ __device__ __forceinline__ void passA_step(const ProbDesc& pd, ProbState* st, in
         // warp 0 takes the previous iteration's decision while the copies are
         // in flight; block 0 commits it
         double a;
-        const int stop = warp_decide(pd.acc + c * kAccBank, st, c, step_cfg(pd), blockIdx.x == 0, &a);
+        const int stop = warp_decide(pd.acc + c * kAccBank, st, c, step_cfg(pd), tile == 0, &a);
         if (threadIdx.x == 0) {
             s_stop = stop;
             s_alpha = a;
-            if (blockIdx.x == 0) st->cur_b = c ^ 1;
+            if (tile == 0) st->cur_b = c ^ 1;
         }
     }
     const bool upd = fin ? true : ld_cg(&st->has_update) != 0;
@@ -43,17 +50,17 @@ __device__ __forceinline__ void passA_step(const ProbDesc& pd, ProbState* st, in
     uint32_t phases = 0;
     const int nst = (pd.tile_rows > kBlock && max_stages<T, KMAX>() == 2) ? 2 : 1;
     const int bank = fin ? (c ^ 1) : c;
-    tile_A<T, KMAX, EXACT>(pd, st, blockIdx.x, upd, alpha, FuseCtl{fin != 0, &s_stop, &s_alpha},
+    tile_A<T, KMAX, EXACT>(pd, st, tile, upd, alpha, FuseCtl{fin != 0, &s_stop, &s_alpha},
                            pd.acc + bank * kAccBank, stage, nst, bars, phases);
 }
 
 // Pass B entry: this iteration's bank (set by pass A); block 0 makes it the
 // pending bank and clears the other one, which the next pass A will fill.
 __device__ __forceinline__ unsigned long long* passB_bank(const ProbDesc& pd, ProbState* st,
-                                                          bool& done) {
+                                                          bool& done, int tile) {
     const int b = ld_cg(&st->cur_b);
     done = ld_cg(&st->done) != 0;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (tile == 0 && threadIdx.x == 0) {
         st->cur = b;
         unsigned long long* z = pd.acc + (b ^ 1) * kAccBank;
 #pragma unroll
@@ -81,7 +88,7 @@ __global__ void __launch_bounds__(kBlock, MODE == MODE_STEP ? passA_min_blocks<T
     k_passA(ProbDesc pd, ProbState* st, T* Gout, uint8_t* chout, int fin) {
     if constexpr (MODE == MODE_STEP) {
         extern __shared__ __align__(128) unsigned char smraw[];
-        passA_step<T, KMAX, false>(pd, st, fin, reinterpret_cast<T*>(smraw));
+        passA_step<T, KMAX, false>(pd, st, fin, reinterpret_cast<T*>(smraw), blockIdx.x);
     } else {
         if (MODE != MODE_GRAD && ld_cg(&st->done)) return;
         const bool upd = ld_cg(&st->has_update) != 0;
@@ -106,7 +113,7 @@ template <typename T, int KMAX>
 __global__ void __launch_bounds__(kBlock, passA_min_blocks<T, KMAX>())
     k_passA_exact(ProbDesc pd, ProbState* st, int fin) {
     extern __shared__ __align__(128) unsigned char smraw[];
-    passA_step<T, KMAX, true>(pd, st, fin, reinterpret_cast<T*>(smraw));
+    passA_step<T, KMAX, true>(pd, st, fin, reinterpret_cast<T*>(smraw), blockIdx.x);
 }
 
 // Pass B: one block per row tile; each adds its tile total to the exact
@@ -114,7 +121,7 @@ __global__ void __launch_bounds__(kBlock, passA_min_blocks<T, KMAX>())
 template <typename T, typename WT, int KMAX>
 __global__ void __launch_bounds__(kBlock) k_passB(ProbDesc pd, ProbState* st) {
     bool done;
-    unsigned long long* accb = passB_bank(pd, st, done);
+    unsigned long long* accb = passB_bank(pd, st, done, blockIdx.x);
     if (done) return;
     extern __shared__ __align__(128) unsigned char smraw[];
     T* sm_lane = reinterpret_cast<T*>(smraw);
@@ -129,7 +136,7 @@ __global__ void __launch_bounds__(kBlock) k_passB(ProbDesc pd, ProbState* st) {
 template <typename T, typename WT, int KMAX, int LC, bool EXACT>
 __device__ __forceinline__ void passB_lc_body(const ProbDesc& pd, ProbState* st) {
     bool done;
-    unsigned long long* accb = passB_bank(pd, st, done);
+    unsigned long long* accb = passB_bank(pd, st, done, blockIdx.x);
     if (done) return;
     extern __shared__ __align__(128) unsigned char smraw[];
     T* sm_lane = reinterpret_cast<T*>(smraw);

@@ -35,7 +35,8 @@ def solve_alone(g, weights, **opts):
 
 @pytest.mark.parametrize("weights", ["f32", "bf16"])
 @pytest.mark.parametrize("schedule,bps,lanes", [("static", 1, 0), ("dynamic", 2, 4),
-                                                ("dynamic", 2, 2), ("static", 0, -1)])
+                                                ("dynamic", 2, 2), ("static", 0, -1),
+                                                ("items", 1, 0), ("items", 0, -1)])
 def test_batch_bitwise_equals_single(weights, schedule, bps, lanes):
     """Batched solves equal single solves bit for bit when both use the same
     lanes per row (the batch's tuned or fixed count, reported by info())."""
@@ -133,14 +134,15 @@ def test_batch_autotune_cache(tmp_path):
     assert os.path.getsize(cache) > 0
 
 
+@pytest.mark.parametrize("schedule", ["dynamic", "items"])
 @pytest.mark.parametrize("kmax_K", [3, 10])
-def test_batch_graph_capture_equals_direct_launches(kmax_K):
-    """The persistent launch runs from a captured CUDA graph by default
-    (FW_GRAPH_REQUIRED), and gives the same bits as direct launches."""
+def test_batch_graph_capture_equals_direct_launches(kmax_K, schedule):
+    """The batch's launches run from a captured CUDA graph by default
+    (FW_GRAPH_REQUIRED), and give the same bits as direct launches."""
     gs = W.batched_blobs(P=5, n_min=300, n_max=20_000, K_min=kmax_K, K_max=kmax_K, seed=17,
                          n_scale=0.2)
     opts = B.fw_seg_default_opts(max_iters=45)
-    kw = dict(blocks_per_sm=2, schedule="dynamic", lanes_per_row=0, iters_per_launch=16)
+    kw = dict(blocks_per_sm=2, schedule=schedule, lanes_per_row=0, iters_per_launch=16)
     with B.Batch(gs, opts, use_graph="required", **kw) as a, \
             B.Batch(gs, opts, use_graph="off", **kw) as d:
         sa, sd = a.solve(), d.solve()
@@ -323,3 +325,29 @@ def test_two_lane_pass_b_bitwise_equals_persistent(weights):
             U, lab, st = solve_alone(g, weights, max_iters=iters, lanes_per_row=2)
             assert np.array_equal(b.U(p), U), (p, g.K)
             assert stats[p].gap == st.gap and stats[p].objective == st.objective, (p, g.K)
+
+
+@pytest.mark.parametrize("schedule", ["dynamic", "items"])
+def test_batch_staggered_stops_over_several_launches(schedule):
+    """Problems that stop at different iterations, in launches of 7
+    iterations: the live set (and so the work list) shrinks between launches,
+    and every problem still equals its single solve bit for bit."""
+    gs = mixed_problems(P=7, seed=23)
+    opts = [B.fw_seg_default_opts(max_iters=m, gap_tol=t, tol_mode="rel")
+            for m, t in ((60, 0.0), (9, 0.0), (200, 5e-2), (33, 0.0), (0, 0.0), (50, 0.0),
+                         (200, 2e-1))]
+    with B.Batch(gs, opts, schedule=schedule, blocks_per_sm=2, lanes_per_row=0,
+                 iters_per_launch=7) as b:
+        # A problem that stops inside pass A must not leave any block waiting
+        # on its bulk copies (each such wait is bounded by 2 s).
+        for _ in range(3):
+            b.reset()
+            t0 = time.time()
+            stats = b.solve()
+            assert time.time() - t0 < 1.5
+        assert b.info().schedule == B.SCHED[schedule]
+        for p, (g, o) in enumerate(zip(gs, opts)):
+            U, lab, st = solve_alone(g, "f32", max_iters=o.max_iters, gap_tol=o.gap_tol,
+                                     tol_mode=o.tol_mode)
+            assert np.array_equal(b.U(p), U), p
+            assert (stats[p].iters, stats[p].status, stats[p].gap) == (st.iters, st.status, st.gap)
