@@ -333,8 +333,10 @@ void fw_batch_destroy(fw_batch *b);
  * while no request waits for admission): the single-problem kernels of
  * fw_seg_solve for one request -- the only resident one, or the oldest when it
  * has at least 131,072 rows (enough to fill the GPU), first in, first out --
- * or else one persistent launch over all of them.  Lone-request epochs run
- * from a captured graph, two kept in flight ahead of the worker thread.
+ * or else one batched epoch over all of them: per-item launches (the
+ * default) or the persistent kernel (FW_SCHED_STATIC / FW_SCHED_DYNAMIC).
+ * Lone-request epochs run from a captured graph, two kept in flight ahead of
+ * the worker thread.
  * Requests that meet their stop rule are harvested
  * (labels copied to the host) and their memory is reused.  Results are
  * bitwise the same as when the request is solved alone.
@@ -347,7 +349,7 @@ typedef struct fw_srv_opts {
     int32_t weight_dtype;      /* FW_WEIGHTS_*, shared by all requests */
     int32_t iters_per_epoch;
     int32_t blocks_per_sm;     /* 0: largest co-resident grid */
-    int32_t schedule;          /* FW_SCHED_* (AUTO: dynamic) */
+    int32_t schedule;          /* FW_SCHED_* (default and AUTO: per-item launches) */
     int32_t spin_budget_ms;
     int32_t reserved;
     void *cuda_stream;         /* stream of the epochs; NULL: the server makes one */

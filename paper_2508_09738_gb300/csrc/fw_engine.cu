@@ -1283,7 +1283,7 @@ fw_status fw_srv_default_opts(fw_srv_opts* o) {
     o->weight_dtype = FW_WEIGHTS_F32;
     o->iters_per_epoch = 16;
     o->blocks_per_sm = 0;
-    o->schedule = FW_SCHED_DYNAMIC;
+    o->schedule = FW_SCHED_ITEMS;
     o->spin_budget_ms = 2000;
     return FW_OK;
 }
@@ -1297,16 +1297,16 @@ fw_status fw_srv_create(fw_srv** out, const fw_srv_opts* opts) {
         else fw_srv_default_opts(&s->so);
         const fw_srv_opts& o = s->so;
         if (o.max_slots < 1 || o.max_K < 2 || o.max_K > 32 || o.iters_per_epoch < 1 ||
-            o.hbm_budget_bytes < 4096)
+            o.hbm_budget_bytes < 4096 || o.schedule < FW_SCHED_AUTO || o.schedule > FW_SCHED_ITEMS)
             return invalid("bad serving options");
         FW_CUDA(cudaGetDevice(&s->device));
         s->eng.use_graph = FW_GRAPH_PREFERRED;
         s->eng.plain_path = true;
         FW_TRY(s->eng.init(o.weight_dtype, o.max_K, o.hbm_budget_bytes, o.max_slots, o.cuda_stream,
                            o.spin_budget_ms > 0 ? o.spin_budget_ms : 2000, o.blocks_per_sm,
-                           (o.schedule == FW_SCHED_STATIC || o.schedule == FW_SCHED_ITEMS)
+                           (o.schedule == FW_SCHED_STATIC || o.schedule == FW_SCHED_DYNAMIC)
                                ? o.schedule
-                               : FW_SCHED_DYNAMIC));
+                               : FW_SCHED_ITEMS));
         s->slot_ticket.assign(size_t(o.max_slots), 0);
         s->slot_epochs.assign(size_t(o.max_slots), 0);
         s->info.pool_bytes = s->eng.ra.cap();

@@ -207,12 +207,16 @@ def requests(seed=21):
     return out
 
 
-def test_server_results_equal_alone():
+@pytest.mark.parametrize("schedule", ["items", "dynamic"])
+def test_server_results_equal_alone(schedule):
+    """Shared epochs run per-item launches (the default) or the persistent
+    kernel; either way each request equals its own solve bit for bit."""
     reqs = requests()
     alone = [solve_alone(g, "f32", **o) for g, o in reqs]
     # a small pool forces queueing and reuse of freed memory
     need = max(B.fw_seg_footprint(g.n, g.nnz, 8, "f32") for g, _ in reqs)
-    with B.Server(hbm_budget_bytes=3 * need, max_slots=4, max_K=8, iters_per_epoch=8) as srv:
+    with B.Server(hbm_budget_bytes=3 * need, max_slots=4, max_K=8, iters_per_epoch=8,
+                  schedule=schedule) as srv:
         tickets = []
         for g, o in reqs:
             tickets.append(srv.submit(g, **o))

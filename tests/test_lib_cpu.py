@@ -54,6 +54,13 @@ def test_defaults_and_footprint(libpath):
     assert bf16 < f32
     # at least CSR + the three iterate arrays
     assert f32 > 4_400_000 * 8 + 3 * 4 * 200_000 * 10
+    # the server's shared epochs default to per-item launches; a schedule
+    # outside the enum is rejected before any device call
+    so = Bd.fw_srv_default_opts()
+    assert so.schedule == Bd.SCHED["items"]
+    with pytest.raises(Bd.FwError) as e:
+        Bd.fw_srv_create(Bd.fw_srv_default_opts(schedule=7))
+    assert e.value.status == Bd.FW_ERR_INVALID_ARG
 
 
 def test_create_without_gpu_reports_cuda_error(libpath):
