@@ -48,6 +48,8 @@ def parse():
     p.add_argument("--iters", type=int, default=0, help="iterations per solve (default: config)")
     p.add_argument("--iters-per-launch", type=int, default=0)
     p.add_argument("--lanes", type=int, default=0)
+    p.add_argument("--class-table", default="auto", choices=["auto", "off", "on"],
+                   help="pass-B form: class table in shared memory (auto: where it pays)")
     p.add_argument("--weights", default="", help="one weight dtype instead of the config's arms")
     p.add_argument("--profile-iters", type=int, default=100)
     p.add_argument("--cpu-seconds", type=float, default=15.0,
@@ -780,8 +782,10 @@ def time_arm(args, B, torch, g, c, weights, iters, stream, flush, clocks, world,
     import torch.distributed as dist
     ipl = args.iters_per_launch or 32     # the library default
     opts = dict(eps=c["eps"], omega0=c["omega0"], weight_dtype=weights, max_iters=iters,
-                iters_per_launch=ipl, lanes_per_row=args.lanes, cuda_stream=stream.cuda_stream)
+                iters_per_launch=ipl, lanes_per_row=args.lanes, class_table=args.class_table,
+                cuda_stream=stream.cuda_stream)
     seg = B.Segmenter(g, **opts)
+    forms = seg.forms().as_dict()
     for _ in range(args.warmup):
         flush.zero_()
         seg.reset()
@@ -813,7 +817,7 @@ def time_arm(args, B, torch, g, c, weights, iters, stream, flush, clocks, world,
     traj = None if (args.no_trajectory or rank != 0) else trajectory(seg, iters)
     seg.close()
     return dict(value=value, t_s=t_s, iters=st.iters, launches=launches, labels=labels, E=E,
-                prof=prof, traj=traj, opts=opts)
+                prof=prof, traj=traj, opts=opts, forms=forms)
 
 
 def arm_record(args, arm, g, c, weights, iters, world, peaks):
@@ -823,7 +827,7 @@ def arm_record(args, arm, g, c, weights, iters, world, peaks):
     rec = {"value": arm["value"], "unit": "iter/s", "weights": weights,
            "ms_per_step": ms_step, "solves_per_s": world * args.steps / arm["t_s"],
            "effective_gbs": by["iteration"] * arm["value"] / world / 1e9,
-           "gpu_launches": arm["launches"], "roofline": roof,
+           "gpu_launches": arm["launches"], "roofline": roof, "kernel_forms": arm["forms"],
            "per_iteration_ms": {
                "timed_step": ms_step / max(1, arm["iters"]),
                "fused_graph": arm["prof"]["per_iter"],

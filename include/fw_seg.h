@@ -84,6 +84,9 @@ typedef struct fw_seg_opts {
     int32_t lanes_per_row;    /* lanes per CSR row in the sparse passes: 0 (auto) or 1,2,4,..,32 */
     int32_t index_width;      /* stored column indices: 0 (auto: 16-bit offsets j - i when every
                                  |j - i| < 2^15, as in pixel grids; else 32-bit) or 32 */
+    int32_t class_table;      /* FW_TABLE_*: pass B reads the 4-bit classes from a copy in
+                                 shared memory (same results; see below) */
+    int32_t reserved;         /* 0 */
     void *cuda_stream;        /* cudaStream_t for all work; NULL: the handle makes one */
 } fw_seg_opts;
 
@@ -102,10 +105,21 @@ typedef struct fw_seg_stats {
 
 typedef struct fw_seg fw_seg;
 
+/* Pass B forms (fw_seg_opts::class_table).  Pass B gathers the class of
+ * every column it reads.  With FW_TABLE_ON, and under FW_TABLE_AUTO for graphs
+ * whose columns are not banded and that have at least one 256-row tile per
+ * SM, it instead runs one 1024-thread block per SM that first copies the
+ * problem's 4-bit class array ((n + 1) / 2 bytes) into shared memory; this
+ * needs an FP32 iterate, K <= 16, 1, 2 or 4 lanes per row, n <= 311,296 and
+ * the array plus the bins within one block's shared memory (n <= 280,574
+ * for 8 < K <= 10 with 2 lanes), else the direct form runs.  Both forms give the
+ * same bits.  FW_TABLE_OFF always runs the direct form. */
+enum { FW_TABLE_AUTO = 0, FW_TABLE_OFF = 1, FW_TABLE_ON = 2 };
+
 /* Fill *opts with defaults: eps 50, omega0 1000 (the paper's network values,
  * Sec. 5.2), gap_tol 0, FW_TOL_ABS, max_iters 500, FP32 weights, L_s, greedy
  * oracle, exact step, refresh_every 0, iters_per_launch 32, lanes auto,
- * index width auto. */
+ * index width auto, class table auto. */
 fw_status fw_seg_default_opts(fw_seg_opts *opts);
 
 /* Device bytes a handle needs for a graph of n nodes, nnz stored entries and
@@ -212,6 +226,20 @@ fw_status fw_seg_profile(fw_seg *h, int32_t iters, double *ms_row_pass, double *
 
 /* Statistics of the handle's current state. */
 fw_status fw_seg_get_stats(fw_seg *h, fw_seg_stats *stats);
+
+/* The kernel forms create chose for the handle (host data only, no device
+ * call): they change no result, only the speed. */
+typedef struct fw_seg_forms {
+    int32_t lanes_per_row;   /* lanes per CSR row of the sparse passes */
+    int32_t index_width;     /* 16: columns stored as offsets j - i; 32: as indices */
+    int32_t class_table;     /* 1: pass B reads the 4-bit classes from shared memory */
+    int32_t table_blocks;    /* blocks of that pass B (0 without it) */
+    int32_t tiles;           /* row tiles of the row passes */
+    int32_t tile_rows;       /* rows per tile (a multiple of 256) */
+    int32_t kmax;            /* class bound the kernels were compiled for (>= K) */
+    int32_t reserved;
+} fw_seg_forms;
+fw_status fw_seg_get_forms(fw_seg *h, fw_seg_forms *forms);
 
 /* Release the handle (NULL is a no-op).  Waits for the handle's stream; the
  * device arrays go back, stream-ordered, to the library's per-device memory

@@ -38,7 +38,17 @@ class fw_seg_opts(ctypes.Structure):
                 ("max_iters", c_int32), ("tol_mode", c_int32), ("weight_dtype", c_int32),
                 ("laplacian", c_int32), ("oracle", c_int32), ("step_rule", c_int32),
                 ("refresh_every", c_int32), ("iters_per_launch", c_int32),
-                ("lanes_per_row", c_int32), ("index_width", c_int32), ("cuda_stream", c_void_p)]
+                ("lanes_per_row", c_int32), ("index_width", c_int32), ("class_table", c_int32),
+                ("reserved", c_int32), ("cuda_stream", c_void_p)]
+
+
+class fw_seg_forms(ctypes.Structure):
+    _fields_ = [("lanes_per_row", c_int32), ("index_width", c_int32), ("class_table", c_int32),
+                ("table_blocks", c_int32), ("tiles", c_int32), ("tile_rows", c_int32),
+                ("kmax", c_int32), ("reserved", c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class fw_seg_stats(ctypes.Structure):
@@ -94,6 +104,7 @@ class fw_srv_info(ctypes.Structure):
 
 
 SCHED = {"auto": 0, "static": 1, "dynamic": 2, "items": 3}
+TABLE = {"auto": 0, "off": 1, "on": 2}
 GRAPH = {"off": 0, "required": 1, "preferred": 2}
 
 _lib = None
@@ -105,6 +116,7 @@ _SIGS = {
     "fw_seg_create": (c_int32, [POINTER(c_void_p), c_int64, c_void_p, c_void_p, c_void_p, c_int32,
                                 c_void_p, POINTER(fw_seg_opts)]),
     "fw_seg_solve": (c_int32, [c_void_p, POINTER(fw_seg_stats)]),
+    "fw_seg_get_forms": (c_int32, [c_void_p, POINTER(fw_seg_forms)]),
     "fw_seg_step": (c_int32, [c_void_p, c_int32, POINTER(fw_seg_stats)]),
     "fw_seg_labels": (c_int32, [c_void_p, c_void_p]),
     "fw_seg_oneshot": (c_int32, [c_void_p, c_void_p, POINTER(c_double)]),
@@ -182,11 +194,12 @@ def fw_seg_default_opts(**kw) -> fw_seg_opts:
 
     String values are accepted for weight_dtype ('f32','bf16','f64'),
     laplacian ('sym','comb'), oracle ('greedy','full'), step_rule
-    ('exact','armijo') and tol_mode ('abs','rel')."""
+    ('exact','armijo'), tol_mode ('abs','rel') and class_table
+    ('auto','off','on')."""
     o = fw_seg_opts()
     _check(lib().fw_seg_default_opts(ctypes.byref(o)))
     maps = dict(weight_dtype=WEIGHTS, laplacian=LAPLACIAN, oracle=ORACLE, step_rule=STEP,
-                tol_mode=TOL)
+                tol_mode=TOL, class_table=TABLE)
     for k, v in kw.items():
         if k in maps and isinstance(v, str):
             v = maps[k][v]
@@ -293,6 +306,12 @@ def fw_seg_get_stats(h: Handle) -> fw_seg_stats:
     return s
 
 
+def fw_seg_get_forms(h: Handle) -> fw_seg_forms:
+    f = fw_seg_forms()
+    _check(lib().fw_seg_get_forms(h.ptr, ctypes.byref(f)))
+    return f
+
+
 def fw_seg_reset(h: Handle) -> None:
     _check(lib().fw_seg_reset(h.ptr))
 
@@ -370,6 +389,9 @@ class Segmenter:
 
     def stats(self):
         return fw_seg_get_stats(self.h)
+
+    def forms(self):
+        return fw_seg_get_forms(self.h)
 
     def refresh(self):
         fw_seg_refresh(self.h)

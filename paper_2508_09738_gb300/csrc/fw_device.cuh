@@ -192,6 +192,21 @@ __device__ __forceinline__ void cp_async_commit() {
 __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.wait_all;" ::: "memory");
 }
+// L2 prefetch of the 128-byte lines of [p, p + bytes) by the block's threads.
+// The caller's array starts on a 128-byte boundary, so every line touched lies
+// in it.
+__device__ __forceinline__ void prefetch_l2_range(const void* p, int64_t bytes) {
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+    const uintptr_t end = a + uintptr_t(bytes);
+    for (uintptr_t q = (a & ~uintptr_t(127)) + uintptr_t(threadIdx.x) * 128u; q < end;
+         q += uintptr_t(blockDim.x) * 128u)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(q));
+}
+__device__ __forceinline__ int ld_shared_u8(uint32_t addr) {
+    uint32_t v;
+    asm volatile("ld.shared.u8 %0, [%1];" : "=r"(v) : "r"(addr));
+    return int(v);
+}
 
 // ------------------------------------------------------- block reductions
 // GB300 executes FP64 at a small fraction of the FP32 rate, so FP64 is used
@@ -873,10 +888,14 @@ enum { kSrcOneHot = 0, kSrcDense = 1, kSrcUhat = 2 };
 // lane each thread's bins are its own row's sums, so the lane-sum stage is
 // skipped and the caller reads sm_lane (a sum over one lane is the value
 // itself, so nothing changes).  EXACT: the problem has exactly KMAX classes.
-template <typename T, typename WT, int KMAX, int SRC, bool RO, int LC = 0, bool EXACT = false>
+// TAB (one-hot only): the 4-bit class pairs are read from a copy of pd.cls4
+// in shared memory (`tab`) instead of being gathered from global memory.
+template <typename T, typename WT, int KMAX, int SRC, bool RO, int LC = 0, bool EXACT = false,
+          bool TAB = false>
 __device__ __forceinline__ void csr_bins(const ProbDesc& pd, const T* __restrict__ X, int base,
                                          int r_end, T* __restrict__ sm_lane,
-                                         T* __restrict__ sm_row) {
+                                         T* __restrict__ sm_row,
+                                         const uint8_t* __restrict__ tab = nullptr) {
     constexpr bool ONEHOT = SRC == kSrcOneHot;
     constexpr int KP = KMAX | 1;
     const int K = EXACT ? KMAX : pd.K;
@@ -958,7 +977,13 @@ __device__ __forceinline__ void csr_bins(const ProbDesc& pd, const T* __restrict
                 const int nt = two ? 8 : 4;
                 if (ONEHOT) {
                     int sj[8];
-                    if constexpr (KMAX <= 16 && RO) {
+                    if constexpr (TAB) {
+                        static_assert(KMAX <= 16, "the class table holds 4-bit classes");
+                        const uint32_t tb = smem_u32(tab);
+#pragma unroll
+                        for (int t = 0; t < 8; ++t)
+                            sj[t] = (ld_shared_u8(tb + uint32_t(cc[t] >> 1)) >> ((cc[t] & 1) << 2)) & 15;
+                    } else if constexpr (KMAX <= 16 && RO) {
                         // 4-bit classes: half the gathered footprint, so more of it
                         // stays in L1.  Only the two-kernel path (RO) keeps them;
                         // the persistent kernel gathers the class bytes.
@@ -1048,6 +1073,47 @@ __host__ __device__ constexpr bool passB_prefetches() {
     return (LC == 1 && KMAX <= 8) || !RO;
 }
 
+// Pass B output of row r from its row sums rs[0..K) (bins of the one-hot
+// product): LS_r = [k = s_r] d_r - rs[k], and, when the row moved (active bit
+// of its choice byte sv), <D_r, LS_r> with D_r = e_{s_r} - U_r added to accq.
+// With PF the row's U values are read from shared memory (uPF[k * kBlock]),
+// else from global memory.
+template <typename T, int KMAX, bool EXACT, bool PF>
+__device__ __forceinline__ void passB_row_out(const ProbDesc& pd, int r, uint8_t sv,
+                                              const T* rs, const T* uPF, T& accq) {
+    const int K = EXACT ? KMAX : pd.K;
+    const int64_t np = pd.npad;
+    const T* __restrict__ Ub = static_cast<const T*>(pd.U);
+    T* __restrict__ LSb = static_cast<T*>(pd.LS);
+    const T* __restrict__ diag = static_cast<const T*>(pd.diag);
+    const int si = sv & 0x7f;
+    const bool act = (sv & kActiveBit) != 0;
+    const T dg = pd.comb ? diag[r] : T(1);
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k)
+        if (k < K) {
+            const T b = rs[k];
+            LSb[k * np + r] = (k == si) ? sub_(dg, b) : -b;
+        }
+    if (act) {
+        // all K loads first (one round trip), then <D_i, LS_i>; LS_i is
+        // re-formed from the row sums rather than kept in registers
+        T u[KMAX];
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k)
+            if (k < K) u[k] = PF ? uPF[k * kBlock] : ld_cg(Ub + k * np + r);
+        T qi = T(0);
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k)
+            if (k < K) {
+                const T b = rs[k];
+                const T ls = (k == si) ? sub_(dg, b) : -b;
+                qi = fma_(sub_(k == si ? T(1) : T(0), u[k]), ls, qi);
+            }
+        accq = add_(accq, qi);
+    }
+}
+
 // Pass B over rows [r_begin, r_end): LS = L S (one-hot S) and sum_i <D_i, LS_i>.
 // sm_pf: passB_prefetch_bytes() of shared memory, 16-byte aligned.  Each warp
 // copies its 32 rows' U values (class-major, 128 bytes per class) and choice
@@ -1061,10 +1127,8 @@ __device__ __forceinline__ void passB_rows(const ProbDesc& pd, int r_begin, int 
     constexpr int kC = 32 / kV;               // copies per class for a warp's 32 rows
     const int K = EXACT ? KMAX : pd.K;
     T* const sm_row = LC == 1 ? sm_lane : sm_row_in;   // one lane: its bins are the row sums
-    const int64_t np = pd.npad;
     const T* __restrict__ Ub = static_cast<const T*>(pd.U);
-    T* __restrict__ LSb = static_cast<T*>(pd.LS);
-    const T* __restrict__ diag = static_cast<const T*>(pd.diag);
+    const int64_t np = pd.npad;
     constexpr bool PF = passB_prefetches<KMAX, RO, LC>();
     T* const sU = sm_pf;
     uint8_t* const sC = reinterpret_cast<uint8_t*>(sm_pf + KMAX * kBlock);
@@ -1085,37 +1149,59 @@ __device__ __forceinline__ void passB_rows(const ProbDesc& pd, int r_begin, int 
             __syncwarp();   // the warp's copies (and its sm_row sums) are visible to all its lanes
         }
         const int r = base + threadIdx.x;
-        if (r < r_end) {
-            const uint8_t sv = PF ? sC[threadIdx.x] : ld_cg(pd.choice + r);
-            const int si = sv & 0x7f;
-            const bool act = (sv & kActiveBit) != 0;
-            const T dg = pd.comb ? diag[r] : T(1);
-#pragma unroll
-            for (int k = 0; k < KMAX; ++k)
-                if (k < K) {
-                    const T b = sm_row[threadIdx.x * KP + k];
-                    LSb[k * np + r] = (k == si) ? sub_(dg, b) : -b;
-                }
-            if (act) {
-                // all K loads first (one round trip), then <D_i, LS_i>; LS_i is
-                // re-formed from the row sums rather than kept in registers
-                T u[KMAX];
-#pragma unroll
-                for (int k = 0; k < KMAX; ++k)
-                    if (k < K) u[k] = PF ? sU[k * kBlock + threadIdx.x] : ld_cg(Ub + k * np + r);
-                T qi = T(0);
-#pragma unroll
-                for (int k = 0; k < KMAX; ++k)
-                    if (k < K) {
-                        const T b = sm_row[threadIdx.x * KP + k];
-                        const T ls = (k == si) ? sub_(dg, b) : -b;
-                        qi = fma_(sub_(k == si ? T(1) : T(0), u[k]), ls, qi);
-                    }
-                accq = add_(accq, qi);
-            }
-        }
+        if (r < r_end)
+            passB_row_out<T, KMAX, EXACT, PF>(pd, r, PF ? sC[threadIdx.x] : ld_cg(pd.choice + r),
+                                              sm_row + threadIdx.x * KP,
+                                              PF ? sU + threadIdx.x : nullptr, accq);
         __syncwarp();   // the warp's bins are reused by the next sub-tile
     }
+}
+
+// ------------------------------------- pass B with a shared class table
+// For graphs whose columns scatter over the whole problem (random-graph
+// models, k-NN graphs), pass B's 4-bit class gathers miss L1 about half the
+// time and their wavefronts fill the L1 data path.  When the problem's class
+// array fits in shared memory next to the bins, one 1024-thread block per SM
+// copies it once and its 32 warps walk the block's row tiles 32 rows at a
+// time, reading classes from shared memory.  Tile totals are formed exactly
+// as passB_rows + block_accumulate form them, so results are bitwise those
+// of the direct kernels.
+constexpr int kTabThreads = 1024;
+constexpr int kTabMaxTiles = 16;   // tiles of one block (the grid is sized for it)
+constexpr int kTabSmemMax = 230400;   // dynamic shared memory of one block (227 KB less the static)
+
+// Shared memory of the bins of kTabThreads threads (the row sums as well
+// unless one lane per row) and of the class table.
+template <typename T, int KMAX>
+__host__ __device__ constexpr size_t tab_bins_bytes(int lanes) {
+    return size_t(lanes == 1 ? 1 : 2) * kTabThreads * (KMAX | 1) * sizeof(T);
+}
+__host__ __device__ inline uint32_t tab_bytes(int n) {
+    return uint32_t((int64_t(n + 1) / 2 + 15) / 16 * 16);
+}
+
+// One 32-row unit of pass B by the calling warp: rows row0 .. row0 + 31 of a
+// 256-row tile whose rows end at r_end.  Lane l takes row row0 + l, the row
+// that lane l of the same warp position takes in passB_rows, and the row
+// arithmetic is the same, so the returned value (the lane's <D_i, LS_i>, or 0)
+// is the one passB_rows accumulates.  sm_lane / sm_row: bins of the whole
+// block (kTabThreads slots); tab: the class table in shared memory.
+template <typename T, typename WT, int KMAX, int LC, bool EXACT>
+__device__ __forceinline__ T passB_unit(const ProbDesc& pd, int row0, int r_end, T* sm_lane,
+                                        T* sm_row_in, const uint8_t* tab) {
+    constexpr int KP = KMAX | 1;
+    T* const sm_row = LC == 1 ? sm_lane : sm_row_in;
+    const int w0 = threadIdx.x & ~31;
+    // csr_bins places the warp's rows at base + (its thread slots)
+    csr_bins<T, WT, KMAX, kSrcOneHot, true, LC, EXACT, true>(pd, nullptr, row0 - w0, r_end,
+                                                             sm_lane, sm_row, tab);
+    T accq = T(0);
+    const int r = row0 + (threadIdx.x & 31);
+    if (r < r_end)
+        passB_row_out<T, KMAX, EXACT, false>(pd, r, ld_cg(pd.choice + r),
+                                             sm_row + threadIdx.x * KP, nullptr, accq);
+    __syncwarp();   // the warp's bins are reused by its next unit
+    return accq;
 }
 
 // OUT = L X for rows [r_begin, r_end) (SoA in and out; OUT may not alias X).

@@ -54,6 +54,9 @@ public:
     virtual void labels(const ProbDesc& pd, int32_t* out, cudaStream_t s) = 0;
     virtual void objective(const ProbDesc& pd, const void* LUf, double* part, cudaStream_t s) = 0;
     virtual cudaError_t configure() = 0;   // dynamic shared-memory limits
+    // Dynamic shared memory of k_passB_tab for this many lanes per row and
+    // rows; 0 when the instantiation has no such form (FP64 iterate, K > 16).
+    virtual size_t tab_smem(int lanes, int64_t n) const = 0;
 };
 
 // Non-template kernels (defined in fw_seg.cu).
@@ -88,6 +91,8 @@ struct ProbLayout {
     bool cls4 = false;
     // store columns as 16-bit offsets when the graph allows (fw_seg_opts::index_width)
     bool allow16 = true;
+    // pass B with the class table in shared memory (fw_seg_opts::class_table)
+    int32_t tab_mode = FW_TABLE_AUTO;
 };
 
 // Host checks (options, row_ptr, labels) and the padded layout.

@@ -159,6 +159,75 @@ __global__ void __launch_bounds__(kBlock, 6) k_passB_lc6(ProbDesc pd, ProbState*
     passB_lc_body<T, WT, KMAX, LC, EXACT>(pd, st);
 }
 
+// Pass B with the class table in shared memory (see passB_unit): one block
+// of kTabThreads threads per SM over a contiguous run of at most
+// kTabMaxTiles 256-row tiles.  The table arrives by bulk copies while the
+// block starts; a copy that does not arrive within the bounded wait raises
+// the problem's error flag and the block adds nothing.
+template <typename T, typename WT, int KMAX, int LC, bool EXACT>
+__global__ void __launch_bounds__(kTabThreads, 1) k_passB_tab(ProbDesc pd, ProbState* st) {
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ T s_part[kTabMaxTiles * (kBlock / 32)];
+    const int G = gridDim.x;
+    const int t0 = int(int64_t(blockIdx.x) * pd.ntiles / G);
+    const int t1 = int(int64_t(blockIdx.x + 1) * pd.ntiles / G);
+    bool done;
+    unsigned long long* accb = passB_bank(pd, st, done, t0);   // block 0 holds tile 0
+    if (done) return;
+    extern __shared__ __align__(128) unsigned char smraw[];
+    T* sm_lane = reinterpret_cast<T*>(smraw);
+    T* sm_row = sm_lane + kTabThreads * (KMAX | 1);   // unused with one lane per row
+    uint8_t* tab = smraw + tab_bins_bytes<T, KMAX>(LC);
+    if (threadIdx.x == 0) {
+        const uint32_t tb = tab_bytes(pd.n);
+        mbar_init(&bar, 1);
+        fence_proxy_async();
+        mbar_expect_tx(&bar, tb);
+        for (uint32_t o = 0; o < tb; o += 32768u)
+            bulk_g2s(tab + o, pd.cls4 + o, min(32768u, tb - o), &bar);
+    }
+    {
+        // while the table arrives, pull the block's CSR slice (row offsets,
+        // columns, weights) into L2, so the warps' dependent loads below wait
+        // on L2 rather than DRAM
+        const int rb = t0 * kBlock, re = min(pd.n, t1 * kBlock);
+        const int e0 = __ldg(pd.rp + rb), e1 = __ldg(pd.rp + re);
+        const int cw = pd.col16 ? 2 : 4;
+        prefetch_l2_range(reinterpret_cast<const char*>(pd.col) + int64_t(e0) * cw,
+                          int64_t(e1 - e0) * cw);
+        prefetch_l2_range(static_cast<const WT*>(pd.val) + e0, int64_t(e1 - e0) * sizeof(WT));
+        prefetch_l2_range(pd.rp + rb, int64_t(re - rb + 1) * 4);
+    }
+    __syncthreads();   // the barrier is initialised before any thread waits on it
+    const bool got = mbar_wait(&bar, 0);
+    if (__syncthreads_or(!got)) {
+        if (!got) mbar_wait(&bar, 0);   // bounded: let copies still in flight land
+        __syncthreads();
+        if (threadIdx.x == 0) atomicExch(&st->err, 1);
+        return;
+    }
+    // warp w takes units w, w + 32, ...; unit u is warp (u % 8) of tile t0 + u / 8
+    const int nunits = (t1 - t0) * (kBlock / 32);
+    for (int u = threadIdx.x >> 5; u < nunits; u += kTabThreads / 32) {
+        const int tile = t0 + u / (kBlock / 32);
+        const int row0 = tile * kBlock + (u % (kBlock / 32)) * 32;
+        const int r_end = min(pd.n, tile * kBlock + kBlock);
+        T x = passB_unit<T, WT, KMAX, LC, EXACT>(pd, row0, r_end, sm_lane, sm_row, tab);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) x = add_(x, __shfl_xor_sync(0xffffffffu, x, off));
+        if ((threadIdx.x & 31) == 0) s_part[u] = x;
+    }
+    __syncthreads();
+    // each tile's total: its 8 warp sums in warp order (block_accumulate's order)
+    if (threadIdx.x < t1 - t0) {
+        T sum = T(0);
+#pragma unroll
+        for (int w = 0; w < kBlock / 32; ++w) sum = add_(sum, s_part[threadIdx.x * (kBlock / 32) + w]);
+        fx_add(acc_slot(accb, (t0 + int(threadIdx.x)) % kAccCopies, kNumA), accb + kAccFlag,
+               double(sum));
+    }
+}
+
 // One thread after pass B: read the iteration's totals (complete after the
 // kernel boundary, in bank cur), run the stop test and the step.  Inside a
 // captured graph only the last iteration ends with it; the others leave the

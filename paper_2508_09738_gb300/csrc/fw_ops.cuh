@@ -15,6 +15,8 @@ public:
     static constexpr bool kExactB = sizeof(T) == 4 && KMAX <= 12;
     // 2 / 4 lanes per row, 5..12 classes, FP32 iterate: the 40-register pass B
     static constexpr bool kBound6 = sizeof(T) == 4 && KMAX >= 8 && KMAX <= 12;
+    // pass B with the class table in shared memory: FP32 iterate, 4-bit classes
+    static constexpr bool kTab = sizeof(T) == 4 && KMAX <= 16;
     size_t elem() const override { return sizeof(T); }
     size_t welem() const override { return sizeof(WT); }
     int kmax() const override { return KMAX; }
@@ -65,6 +67,15 @@ public:
                 if (e != cudaSuccess) return e;
             }
         }
+        if constexpr (kTab) {
+            for (auto f : {k_passB_tab<T, WT, KMAX, 1, false>, k_passB_tab<T, WT, KMAX, 2, false>,
+                           k_passB_tab<T, WT, KMAX, 4, false>, k_passB_tab<T, WT, KMAX, 1, true>,
+                           k_passB_tab<T, WT, KMAX, 2, true>, k_passB_tab<T, WT, KMAX, 4, true>}) {
+                e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kTabSmemMax);
+                if (e != cudaSuccess) return e;
+            }
+        }
         e = cudaFuncSetAttribute(k_spmm_hat<T, WT, KMAX>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem()));
         if (e != cudaSuccess) return e;
@@ -102,7 +113,29 @@ public:
         else
             k_passB_lc<T, WT, KMAX, 4, EXACT><<<g, kBlock, smemB_lc<4>(), s>>>(pd, st);
     }
+    size_t tab_smem(int lanes, int64_t n) const override {
+        if constexpr (kTab) return tab_bins_bytes<T, KMAX>(lanes) + tab_bytes(int(n));
+        return 0;
+    }
+    template <bool EXACT>
+    void passB_tab(const ProbDesc& pd, ProbState* st, cudaStream_t s) {
+        const unsigned g = unsigned(pd.tab_grid);
+        const size_t sm = tab_smem(pd.lanes, pd.n);
+        if (pd.lanes == 1)
+            k_passB_tab<T, WT, KMAX, 1, EXACT><<<g, kTabThreads, sm, s>>>(pd, st);
+        else if (pd.lanes == 2)
+            k_passB_tab<T, WT, KMAX, 2, EXACT><<<g, kTabThreads, sm, s>>>(pd, st);
+        else
+            k_passB_tab<T, WT, KMAX, 4, EXACT><<<g, kTabThreads, sm, s>>>(pd, st);
+    }
     void passB(const ProbDesc& pd, ProbState* st, cudaStream_t s) override {
+        if constexpr (kTab) {
+            if (pd.tab_grid > 0) {   // choose_tab checked lanes, tiles and the fit
+                if (pd.K == KMAX) passB_tab<true>(pd, st, s);
+                else passB_tab<false>(pd, st, s);
+                return;
+            }
+        }
         if (pd.lanes != 1 && pd.lanes != 2 && pd.lanes != 4) {
             k_passB<T, WT, KMAX><<<unsigned(pd.ntiles), kBlock, smemB_lc<0>(), s>>>(pd, st);
             return;

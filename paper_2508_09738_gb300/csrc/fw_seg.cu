@@ -29,8 +29,9 @@ const char* last_error_text();
 
 using namespace fw;
 
-static_assert(sizeof(fw_seg_opts) == 72, "fw_seg_opts ABI");
+static_assert(sizeof(fw_seg_opts) == 80, "fw_seg_opts ABI");
 static_assert(sizeof(fw_seg_stats) == 64, "fw_seg_stats ABI");
+static_assert(sizeof(fw_seg_forms) == 32, "fw_seg_forms ABI");
 
 static fw_status invalid(const std::string& m) {
     set_error(m);
@@ -312,6 +313,7 @@ fw_status fw_seg_default_opts(fw_seg_opts* o) {
     o->refresh_every = 0;
     o->iters_per_launch = 32;
     o->lanes_per_row = 0;
+    o->class_table = FW_TABLE_AUTO;
     o->cuda_stream = nullptr;
     return FW_OK;
 }
@@ -718,6 +720,19 @@ fw_status fw_seg_get_stats(fw_seg* h, fw_seg_stats* stats) {
     if (!h || !stats) return invalid("NULL argument");
     FW_TRY(read_state(h));
     fill_stats(h, stats, 0.f);
+    return FW_OK;
+}
+
+fw_status fw_seg_get_forms(fw_seg* h, fw_seg_forms* f) {
+    if (!h || !f) return invalid("NULL argument");
+    std::memset(f, 0, sizeof(*f));
+    f->lanes_per_row = h->pd.lanes;
+    f->index_width = h->pd.col16 ? 16 : 32;
+    f->class_table = h->pd.tab_grid > 0 ? 1 : 0;
+    f->table_blocks = h->pd.tab_grid;
+    f->tiles = h->pd.ntiles;
+    f->tile_rows = h->pd.tile_rows;
+    f->kmax = h->ops ? h->ops->kmax() : 0;
     return FW_OK;
 }
 

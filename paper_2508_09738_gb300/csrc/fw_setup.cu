@@ -242,6 +242,8 @@ fw_status check_opts(const fw_seg_opts& o) {
     if (o.iters_per_launch < 1 || o.iters_per_launch > 4096)
         return invalid("iters_per_launch must be in [1, 4096]");
     if (o.index_width != 0 && o.index_width != 32) return invalid("index_width must be 0 or 32");
+    if (o.class_table < FW_TABLE_AUTO || o.class_table > FW_TABLE_ON)
+        return invalid("class_table must be FW_TABLE_AUTO, FW_TABLE_OFF or FW_TABLE_ON");
     const int L = o.lanes_per_row;
     if (L != 0 && (L < 1 || L > 32 || (L & (L - 1)) != 0))
         return invalid("lanes_per_row must be 0 or a power of two <= 32");
@@ -328,6 +330,7 @@ fw_status plan_problem(const HostGraph& g, const fw_seg_opts& o, ProbLayout& lay
     lay.ntiles = int32_t((n + lay.tile_rows - 1) / lay.tile_rows);
     lay.lanes = o.lanes_per_row ? o.lanes_per_row : default_lanes(double(acc) / double(n));
     lay.allow16 = o.index_width != 32;
+    lay.tab_mode = o.class_table;
     return FW_OK;
 }
 
@@ -505,6 +508,29 @@ fw_status upload_inputs(const HostGraph& g, Upload& up) {
     return FW_OK;
 }
 
+// Pass B with the class table in shared memory (k_passB_tab): where the
+// table and the bins fit one block's shared memory, the tiles are single
+// 256-row sub-tiles and the lane count has a compiled form.  AUTO takes it for
+// graphs whose columns are not banded (their class gathers miss L1; banded
+// ones hit it) and that have at least one tile per SM; ON wherever it fits.
+static fw_status choose_tab(Ops* ops, const ProbLayout& lay, ProbDesc& pd) {
+    pd.tab_grid = 0;
+    if (lay.tab_mode == FW_TABLE_OFF || !pd.cls4 || lay.tile_rows != kBlock) return FW_OK;
+    if (lay.lanes != 1 && lay.lanes != 2 && lay.lanes != 4) return FW_OK;
+    const size_t need = ops->tab_smem(lay.lanes, lay.n);
+    if (need == 0 || need > size_t(kTabSmemMax)) return FW_OK;
+    int dev = 0, sms = 0, optin = 0;
+    FW_CUDA(cudaGetDevice(&dev));
+    FW_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    FW_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if (need + 2048 > size_t(optin)) return FW_OK;
+    if (lay.tab_mode == FW_TABLE_AUTO && (pd.col16 || lay.ntiles < sms)) return FW_OK;
+    const int grid = std::max(std::min(sms, lay.ntiles),
+                              (lay.ntiles + kTabMaxTiles - 1) / kTabMaxTiles);
+    pd.tab_grid = grid;
+    return FW_OK;
+}
+
 fw_status assemble_problem(Ops* ops, const HostGraph& g, const ProbLayout& lay, ProbDesc& pd,
                            ProbState* st, cudaStream_t s) {
     Upload up(s);
@@ -558,6 +584,7 @@ fw_status assemble_uploaded(Ops* ops, Upload& up, const ProbLayout& lay, ProbDes
     // banded graphs (pixel grids, meshes) keep 16-bit column offsets: the
     // same entries in half the column bytes of every sparse pass
     pd.col16 = (lay.allow16 && !(err & 8)) ? 1 : 0;
+    FW_TRYS(choose_tab(ops, lay, pd));
     if (!pd.comb) k_inv_sqrt<<<gr, kBlock, 0, s>>>(n, d_deg);
     ops->build(n, d_rp, d_col, d_w, d_deg, pd.rp, const_cast<int32_t*>(pd.col),
                const_cast<void*>(pd.val), const_cast<void*>(pd.diag), pd.comb, pd.col16, s);

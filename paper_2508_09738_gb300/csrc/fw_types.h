@@ -58,6 +58,9 @@ struct ProbDesc {
     int32_t tol_mode;    // 0 abs, 1 relative to g_0
     int32_t max_iters;
     int32_t col16;       // 1: col holds 16-bit offsets (every |j - i| < 2^15)
+    int32_t tab_grid;    // > 0: pass B runs k_passB_tab on this many blocks (class table
+                         // in shared memory); 0: the direct pass-B kernels
+    int32_t pad_;
     double inv_eps;      // 1/eps (0 when eps = +inf)
     double omega0;       // fidelity weight
     double gap_tol;
