@@ -456,8 +456,10 @@ def run_batched(args, rank, world, local, emit=True):
         "oracle_sample": sample,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                      "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                     "kernel": "k_persistent", "peak_source": peaks["source"],
-                     "algorithmic_bytes": "sum over problems of iteration bytes x iterations"},
+                     "kernel": ("k_itemA + k_itemB" if info.get("schedule") == 3 else "k_persistent"),
+                     "peak_source": peaks["source"],
+                     "algorithmic_bytes": "sum over problems of iteration bytes x iterations; "
+                                          "whole solves timed (all of the batch's kernels)"},
         "setup_s": {"generate": gen_s, "create_and_tune": create_s},
     }
     bt.close()
