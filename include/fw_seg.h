@@ -359,10 +359,12 @@ void fw_batch_destroy(fw_batch *b);
  * stream while the current epoch runs, and joins the next epoch.  An epoch is
  * iters_per_epoch iterations of every resident request (four times as many
  * while no request waits for admission): the single-problem kernels of
- * fw_seg_solve for one request -- the only resident one, or the oldest when it
- * has at least 131,072 rows (enough to fill the GPU), first in, first out --
- * or else one batched epoch over all of them: per-item launches (the
- * default) or the persistent kernel (FW_SCHED_STATIC / FW_SCHED_DYNAMIC).
+ * fw_seg_solve for one request -- the only resident one, the oldest when it
+ * has at least 131,072 rows (enough to fill the GPU), first in, first out, or
+ * the only resident below that size -- or else one batched epoch over the
+ * residents below that size (a large one waits until it is the oldest):
+ * per-item launches (the default) or the persistent kernel
+ * (FW_SCHED_STATIC / FW_SCHED_DYNAMIC).
  * Lone-request epochs run from a captured graph, two kept in flight ahead of
  * the worker thread.
  * Requests that meet their stop rule are harvested

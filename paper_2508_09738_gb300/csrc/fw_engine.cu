@@ -364,13 +364,18 @@ public:
         return restart_problem(ops.get(), slots[size_t(s)].pd, d_state + s, false, st);
     }
 
-    // Work list of the live problems (used and not done).
+    // Problems of at least this many rows stay out of batched launches (the
+    // server runs them alone); the batch API keeps every problem.
+    int64_t shared_max_rows = INT64_MAX;
+
+    // Work list of the live problems (used, not done, below shared_max_rows).
     int build_work() {
         std::vector<int2> w;
         std::vector<int> live;
         bool two = false;
         for (int s = 0; s < nslots(); ++s) {
             if (!slots[size_t(s)].used || h_state[s].done) continue;
+            if (slots[size_t(s)].lay.n >= shared_max_rows) continue;
             live.push_back(s);
             two = two || slots[size_t(s)].lay.tile_rows > kBlock;
             for (int t = 0; t < slots[size_t(s)].lay.ntiles; ++t) w.push_back(make_int2(s, t));
@@ -1195,17 +1200,27 @@ void fw_srv::loop() {
         const int iters = so.iters_per_epoch * (waiting ? 1 : 4);
         // a lone resident, or the oldest resident when it is large enough to
         // fill the GPU by itself, runs alone on the single-problem kernels
-        // (first in, first out); otherwise one persistent launch iterates all
+        // (first in, first out); otherwise one batched epoch iterates the
+        // small residents (the large ones wait for their turn as the oldest:
+        // in a shared epoch every iteration would cost the small ones the
+        // large one's time), and a single small one runs alone too
         int lone = e.lone_live();
         if (lone < 0) {
             uint64_t first = UINT64_MAX;
-            int oldest = -1;
-            for (int q = 0; q < e.nslots(); ++q)
-                if (e.slots[size_t(q)].used && !e.h_state[q].done && slot_ticket[size_t(q)] < first) {
+            int oldest = -1, small = -1, nsmall = 0;
+            for (int q = 0; q < e.nslots(); ++q) {
+                if (!e.slots[size_t(q)].used || e.h_state[q].done) continue;
+                if (slot_ticket[size_t(q)] < first) {
                     first = slot_ticket[size_t(q)];
                     oldest = q;
                 }
+                if (e.slots[size_t(q)].lay.n < kAloneRows) {
+                    small = q;
+                    ++nsmall;
+                }
+            }
             if (oldest >= 0 && e.slots[size_t(oldest)].lay.n >= kAloneRows) lone = oldest;
+            else if (nsmall == 1) lone = small;
         }
         bool piped = false;
         fw_status rc = lone >= 0 ? e.lone_queue(lone, iters, &piped) : FW_OK;
@@ -1302,6 +1317,7 @@ fw_status fw_srv_create(fw_srv** out, const fw_srv_opts* opts) {
         FW_CUDA(cudaGetDevice(&s->device));
         s->eng.use_graph = FW_GRAPH_PREFERRED;
         s->eng.plain_path = true;
+        s->eng.shared_max_rows = kAloneRows;   // large requests run alone, in arrival order
         FW_TRY(s->eng.init(o.weight_dtype, o.max_K, o.hbm_budget_bytes, o.max_slots, o.cuda_stream,
                            o.spin_budget_ms > 0 ? o.spin_budget_ms : 2000, o.blocks_per_sm,
                            (o.schedule == FW_SCHED_STATIC || o.schedule == FW_SCHED_DYNAMIC)

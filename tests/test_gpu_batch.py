@@ -288,10 +288,13 @@ def test_server_lone_requests_and_wait_any():
     assert info.completed == len(reqs) and info.failed == 0
 
 
-def test_server_large_oldest_runs_alone_equal_results():
+@pytest.mark.parametrize("order", ["large_first", "small_first"])
+def test_server_large_oldest_runs_alone_equal_results(order):
     """The oldest resident request runs alone when it has at least 2^17 rows;
-    small requests behind it share persistent launches once it is done.
-    Every result equals the request solved alone, bit for bit."""
+    smaller residents share batched epochs without the large ones, which wait
+    until they are the oldest (small_first: two small requests share epochs
+    while two large ones wait).  Every result equals the request solved alone,
+    bit for bit."""
     reqs = [(W.voronoi_image(side=400, K=4, seed=71, label_frac=0.005),
              dict(max_iters=120, omega0=1e5)),
             (W.blobs_knn(n=900, K=3, seed=72), dict(max_iters=90)),
@@ -300,6 +303,8 @@ def test_server_large_oldest_runs_alone_equal_results():
             (W.blobs_knn(n=1500, K=6, seed=74), dict(max_iters=150)),
             (W.voronoi_image(side=50, K=3, seed=75, label_frac=0.02), dict(max_iters=70))]
     assert reqs[0][0].n >= 1 << 17 and reqs[2][0].n >= 1 << 17
+    if order == "small_first":
+        reqs = [reqs[1], reqs[3], reqs[0], reqs[2], reqs[4]]
     alone = [solve_alone(g, "f32", **o) for g, o in reqs]
     with B.Server(hbm_budget_bytes=2 << 30, max_slots=8, max_K=8, iters_per_epoch=8) as srv:
         tickets = [srv.submit(g, **o) for g, o in reqs]
