@@ -854,8 +854,11 @@ __device__ __forceinline__ int passA_staged(const ProbDesc& pd, int r_begin, int
 
 // Stage 1 of the sparse passes: for each row of a 256-row sub-tile, `L` lanes
 // walk the padded CSR row in 4-entry chunks and accumulate into per-lane bins
-// in shared memory (`sm_lane`, one KP-strided slot per thread); the lanes of a
-// row then add their slots in lane order into `sm_row[row]`.  Warp w handles
+// in shared memory (`sm_lane`, class-major: class k of thread slot t at
+// k * S + t, S the block's thread count, so the 32 lanes of a warp always hit
+// 32 different banks whatever classes they update); the lanes of a row then
+// add their slots in lane order into `sm_row` (class k of row slot r at
+// k * S + r).  Warp w handles
 // exactly rows 32w .. 32w+31 of the sub-tile (32/L rows at a time), so the
 // row sums never leave the warp: __syncwarp orders them, and the caller needs
 // no block barrier before thread t reads sm_row[t].
@@ -891,13 +894,12 @@ enum { kSrcOneHot = 0, kSrcDense = 1, kSrcUhat = 2 };
 // TAB (one-hot only): the 4-bit class pairs are read from a copy of pd.cls4
 // in shared memory (`tab`) instead of being gathered from global memory.
 template <typename T, typename WT, int KMAX, int SRC, bool RO, int LC = 0, bool EXACT = false,
-          bool TAB = false>
+          bool TAB = false, int S = kBlock>
 __device__ __forceinline__ void csr_bins(const ProbDesc& pd, const T* __restrict__ X, int base,
                                          int r_end, T* __restrict__ sm_lane,
                                          T* __restrict__ sm_row,
                                          const uint8_t* __restrict__ tab = nullptr) {
     constexpr bool ONEHOT = SRC == kSrcOneHot;
-    constexpr int KP = KMAX | 1;
     const int K = EXACT ? KMAX : pd.K;
     const int L = LC ? LC : pd.lanes;
     const int64_t np = pd.npad;
@@ -911,7 +913,7 @@ __device__ __forceinline__ void csr_bins(const ProbDesc& pd, const T* __restrict
     const int lane = tid & (L - 1);
     const int grp = tid / L;                    // lane group: its lanes are adjacent threads
     const int wrow = (tid & ~31) + (tid & 31) / L;
-    T* my = sm_lane + tid * KP;
+    T* my = sm_lane + tid;   // my[k * S]: this thread's bin of class k
     for (int j = 0; j < L; ++j) {
         const int rl = wrow + (32 / L) * j;     // a row of this warp's 32
         const int r = base + rl;
@@ -921,7 +923,7 @@ __device__ __forceinline__ void csr_bins(const ProbDesc& pd, const T* __restrict
         if (ONEHOT) {
 #pragma unroll
             for (int k = 0; k < KMAX; ++k)
-                if (k < K) my[k] = T(0);
+                if (k < K) my[k * S] = T(0);
         }
         if (r < r_end) {
             const int e0 = __ldg(rp + r);
@@ -1002,7 +1004,7 @@ __device__ __forceinline__ void csr_bins(const ProbDesc& pd, const T* __restrict
                     }
 #pragma unroll
                     for (int t = 0; t < 8; ++t)
-                        if (t < nt) my[sj[t]] = add_(my[sj[t]], v[t]);
+                        if (t < nt) my[sj[t] * S] = add_(my[sj[t] * S], v[t]);
                 } else if constexpr (SRC == kSrcDense) {
 #pragma unroll
                     for (int t = 0; t < 8; ++t) {
@@ -1043,14 +1045,14 @@ __device__ __forceinline__ void csr_bins(const ProbDesc& pd, const T* __restrict
         if (!ONEHOT) {
 #pragma unroll
             for (int k = 0; k < KMAX; ++k)
-                if (k < K) my[k] = acc[k];
+                if (k < K) my[k * S] = acc[k];
         }
         if constexpr (LC != 1) {
             __syncwarp();
             for (int k = lane; k < K; k += L) {
                 T s = T(0);
-                for (int l2 = 0; l2 < L; ++l2) s = add_(s, sm_lane[(grp * L + l2) * KP + k]);
-                sm_row[rl * KP + k] = s;
+                for (int l2 = 0; l2 < L; ++l2) s = add_(s, sm_lane[k * S + grp * L + l2]);
+                sm_row[k * S + rl] = s;
             }
             __syncwarp();
         }
@@ -1073,12 +1075,12 @@ __host__ __device__ constexpr bool passB_prefetches() {
     return (LC == 1 && KMAX <= 8) || !RO;
 }
 
-// Pass B output of row r from its row sums rs[0..K) (bins of the one-hot
-// product): LS_r = [k = s_r] d_r - rs[k], and, when the row moved (active bit
-// of its choice byte sv), <D_r, LS_r> with D_r = e_{s_r} - U_r added to accq.
-// With PF the row's U values are read from shared memory (uPF[k * kBlock]),
-// else from global memory.
-template <typename T, int KMAX, bool EXACT, bool PF>
+// Pass B output of row r from its row sums rs[k * S], k < K (bins of the
+// one-hot product): LS_r = [k = s_r] d_r - rs[k], and, when the row moved
+// (active bit of its choice byte sv), <D_r, LS_r> with D_r = e_{s_r} - U_r
+// added to accq.  With PF the row's U values are read from shared memory
+// (uPF[k * kBlock]), else from global memory.
+template <typename T, int KMAX, bool EXACT, bool PF, int S = kBlock>
 __device__ __forceinline__ void passB_row_out(const ProbDesc& pd, int r, uint8_t sv,
                                               const T* rs, const T* uPF, T& accq) {
     const int K = EXACT ? KMAX : pd.K;
@@ -1092,7 +1094,7 @@ __device__ __forceinline__ void passB_row_out(const ProbDesc& pd, int r, uint8_t
 #pragma unroll
     for (int k = 0; k < KMAX; ++k)
         if (k < K) {
-            const T b = rs[k];
+            const T b = rs[k * S];
             LSb[k * np + r] = (k == si) ? sub_(dg, b) : -b;
         }
     if (act) {
@@ -1106,7 +1108,7 @@ __device__ __forceinline__ void passB_row_out(const ProbDesc& pd, int r, uint8_t
 #pragma unroll
         for (int k = 0; k < KMAX; ++k)
             if (k < K) {
-                const T b = rs[k];
+                const T b = rs[k * S];
                 const T ls = (k == si) ? sub_(dg, b) : -b;
                 qi = fma_(sub_(k == si ? T(1) : T(0), u[k]), ls, qi);
             }
@@ -1122,7 +1124,6 @@ __device__ __forceinline__ void passB_row_out(const ProbDesc& pd, int r, uint8_t
 template <typename T, typename WT, int KMAX, bool RO, int LC = 0, bool EXACT = false>
 __device__ __forceinline__ void passB_rows(const ProbDesc& pd, int r_begin, int r_end, T& accq,
                                            T* sm_lane, T* sm_row_in, T* sm_pf) {
-    constexpr int KP = KMAX | 1;
     constexpr int kV = 16 / int(sizeof(T));   // values per 16-byte copy
     constexpr int kC = 32 / kV;               // copies per class for a warp's 32 rows
     const int K = EXACT ? KMAX : pd.K;
@@ -1151,7 +1152,7 @@ __device__ __forceinline__ void passB_rows(const ProbDesc& pd, int r_begin, int 
         const int r = base + threadIdx.x;
         if (r < r_end)
             passB_row_out<T, KMAX, EXACT, PF>(pd, r, PF ? sC[threadIdx.x] : ld_cg(pd.choice + r),
-                                              sm_row + threadIdx.x * KP,
+                                              sm_row + threadIdx.x,
                                               PF ? sU + threadIdx.x : nullptr, accq);
         __syncwarp();   // the warp's bins are reused by the next sub-tile
     }
@@ -1189,17 +1190,16 @@ __host__ __device__ inline uint32_t tab_bytes(int n) {
 template <typename T, typename WT, int KMAX, int LC, bool EXACT>
 __device__ __forceinline__ T passB_unit(const ProbDesc& pd, int row0, int r_end, T* sm_lane,
                                         T* sm_row_in, const uint8_t* tab) {
-    constexpr int KP = KMAX | 1;
     T* const sm_row = LC == 1 ? sm_lane : sm_row_in;
     const int w0 = threadIdx.x & ~31;
     // csr_bins places the warp's rows at base + (its thread slots)
-    csr_bins<T, WT, KMAX, kSrcOneHot, true, LC, EXACT, true>(pd, nullptr, row0 - w0, r_end,
-                                                             sm_lane, sm_row, tab);
+    csr_bins<T, WT, KMAX, kSrcOneHot, true, LC, EXACT, true, kTabThreads>(
+        pd, nullptr, row0 - w0, r_end, sm_lane, sm_row, tab);
     T accq = T(0);
     const int r = row0 + (threadIdx.x & 31);
     if (r < r_end)
-        passB_row_out<T, KMAX, EXACT, false>(pd, r, ld_cg(pd.choice + r),
-                                             sm_row + threadIdx.x * KP, nullptr, accq);
+        passB_row_out<T, KMAX, EXACT, false, kTabThreads>(pd, r, ld_cg(pd.choice + r),
+                                                          sm_row + threadIdx.x, nullptr, accq);
     __syncwarp();   // the warp's bins are reused by its next unit
     return accq;
 }
@@ -1209,7 +1209,6 @@ template <typename T, typename WT, int KMAX, int SRC = kSrcDense>
 __device__ __forceinline__ void spmm_rows(const ProbDesc& pd, const T* __restrict__ X,
                                           T* __restrict__ OUT, int r_begin, int r_end, T* sm_lane,
                                           T* sm_row) {
-    constexpr int KP = KMAX | 1;
     const int K = pd.K;
     const int64_t np = pd.npad;
     const T* __restrict__ diag = static_cast<const T*>(pd.diag);
@@ -1225,7 +1224,7 @@ __device__ __forceinline__ void spmm_rows(const ProbDesc& pd, const T* __restric
             for (int k = 0; k < KMAX; ++k)
                 if (k < K)
                     OUT[k * np + r] = sub_(mul_(dg, ld_cg(X + k * np + r)),
-                                           sm_row[threadIdx.x * KP + k]);
+                                           sm_row[k * kBlock + threadIdx.x]);
         }
         __syncwarp();
     }
@@ -1239,7 +1238,6 @@ __device__ __forceinline__ void spmm_rows(const ProbDesc& pd, const T* __restric
 template <typename T, typename WT, int KMAX>
 __device__ __forceinline__ void osfw_rows(const ProbDesc& pd, int32_t* __restrict__ labels,
                                           int r_begin, int r_end, T* sm_lane, T* sm_row) {
-    constexpr int KP = KMAX | 1;
     const int K = pd.K;
     const T* __restrict__ diag = static_cast<const T*>(pd.diag);
     const T c2 = c2_of<T>(pd);
@@ -1259,7 +1257,7 @@ __device__ __forceinline__ void osfw_rows(const ProbDesc& pd, int32_t* __restric
             for (int k = 0; k < KMAX; ++k)
                 if (k < K) {
                     const T u = uhat_val<T>(f, k, unif);
-                    const T lu = sub_(mul_(dg, u), sm_row[threadIdx.x * KP + k]);
+                    const T lu = sub_(mul_(dg, u), sm_row[k * kBlock + threadIdx.x]);
                     binary = binary && (u == T(0) || u == T(1));
                     if (first_one < 0 && u == T(1)) first_one = k;
                     T gk = fma_(-c2, u, lu);
