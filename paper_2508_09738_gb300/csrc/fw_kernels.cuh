@@ -15,24 +15,30 @@ __device__ __forceinline__ void passA_step(const ProbDesc& pd, ProbState* st, in
                                            int tile) {
     __shared__ __align__(8) uint64_t bars[2];
     __shared__ double s_alpha;
-    __shared__ int s_stop, s_done;
+    __shared__ int s_stop, s_done, s_cur;
     // Block 0 of this launch may commit a stop (done = 1) while other blocks
-    // start: one thread reads the flag and the whole block follows it, so no
-    // block splits between leaving and waiting on the bulk copies.
-    if (threadIdx.x == 0) s_done = ld_cg(&st->done);
-    __syncthreads();
-    if (s_done) return;
-    const int c = ld_cg(&st->cur);
+    // start: one thread reads the flag (and the parity) and the whole block
+    // follows it, so no block splits between leaving and waiting on the bulk
+    // copies; that thread issues the copies as soon as it knows.
     if (threadIdx.x == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
-        if (fin) {   // the first copies go out at once (a step is always pending)
-            const int r0 = tile * pd.tile_rows;
-            stage_issue<T, KMAX>(pd, r0, min(kBlock, pd.n - r0), true, stage, &bars[0]);
-        } else if (tile == 0) {
-            st->cur_b = c;
+        const int d = ld_cg(&st->done);
+        const int c0 = ld_cg(&st->cur);
+        s_done = d;
+        s_cur = c0;
+        if (!d) {
+            mbar_init(&bars[0], 1);
+            mbar_init(&bars[1], 1);
+            if (fin) {   // the first copies go out at once (a step is always pending)
+                const int r0 = tile * pd.tile_rows;
+                stage_issue<T, KMAX>(pd, r0, min(kBlock, pd.n - r0), true, stage, &bars[0]);
+            } else if (tile == 0) {
+                st->cur_b = c0;
+            }
         }
     }
+    __syncthreads();
+    if (s_done) return;
+    const int c = s_cur;
     if (fin && threadIdx.x < 32) {
         // warp 0 takes the previous iteration's decision while the copies are
         // in flight; block 0 commits it
