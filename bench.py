@@ -758,7 +758,7 @@ def compare_golden(gold, labels, E_gpu, traj, truth):
     return d
 
 
-def roofline_of(prof, g, weights, workload, peaks):
+def roofline_of(prof, g, weights, workload, peaks, forms=None):
     wb = {"f32": 4, "bf16": 2, "f64": 8}[weights]
     tb = 8 if weights == "f64" else 4
     by = bytes_per_unit(g.n, g.nnz, g.K, wb, tb, column_bytes(g))
@@ -770,6 +770,9 @@ def roofline_of(prof, g, weights, workload, peaks):
     return {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": ncu_traffic(kernel, key),
             "kernel": kernel, "peak_source": peaks["source"],
+            "kernel_form": (("k_passB_tab (class table in shared memory)"
+                             if forms and forms.get("class_table") else "k_passB_lc / k_passB")
+                            if kernel == "k_passB" else "k_passA"),
             "algorithmic_bytes_per_launch": by[dom],
             "timing": "CUDA events on the solver's stream around a captured graph of "
                       "back-to-back launches of the kernel" if prof["in_graph"] else
@@ -824,7 +827,7 @@ def time_arm(args, B, torch, g, c, weights, iters, stream, flush, clocks, world,
 
 def arm_record(args, arm, g, c, weights, iters, world, peaks):
     """The JSON fields of one timed weight dtype."""
-    roof, by = roofline_of(arm["prof"], g, weights, args.workload, peaks)
+    roof, by = roofline_of(arm["prof"], g, weights, args.workload, peaks, arm.get("forms"))
     ms_step = 1000.0 * arm["t_s"] / args.steps
     rec = {"value": arm["value"], "unit": "iter/s", "weights": weights,
            "ms_per_step": ms_step, "solves_per_s": world * args.steps / arm["t_s"],
