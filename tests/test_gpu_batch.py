@@ -288,6 +288,33 @@ def test_server_lone_requests_and_wait_any():
     assert info.completed == len(reqs) and info.failed == 0
 
 
+def test_server_lone_request_takes_class_table_form():
+    """A served request large enough for the class-table pass B (scattered
+    columns, more tiles than SMs) runs alone on the single-problem kernels
+    with that form when it is the only resident, and equals its own solve
+    bit for bit; so does it behind a small request, with which it shares
+    per-item epochs (the direct pass-B code) before it finishes alone."""
+    g = W.sbm(n=50_000, K=5, deg_in=16.0, deg_out=3.0, label_frac=0.01, seed=81)
+    small = W.blobs_knn(n=700, K=3, seed=82)
+    o = dict(max_iters=150, gap_tol=1e-4, tol_mode="rel")
+    with B.Segmenter(g, weight_dtype="f32", **o) as s:
+        assert s.forms().class_table == 1
+    U, lab, st = solve_alone(g, "f32", **o)
+    _, lab_small, st_small = solve_alone(small, "f32", **o)
+    with B.Server(hbm_budget_bytes=1 << 30, max_slots=4, max_K=8, iters_per_epoch=8) as srv:
+        for first in (None, small):
+            tk = [srv.submit(first, **o)] if first is not None else []
+            t = srv.submit(g, **o)
+            rc, lab_s, st_s = srv.wait(t, g.n, timeout_ms=60_000)
+            assert rc == st.status and np.array_equal(lab_s, lab)
+            assert (st_s.iters, st_s.gap, st_s.objective) == (st.iters, st.gap, st.objective)
+            for t2 in tk:
+                rc2, lab2, st2 = srv.wait(t2, small.n, timeout_ms=60_000)
+                assert rc2 == st_small.status and np.array_equal(lab2, lab_small)
+        info = srv.info()
+    assert info.failed == 0
+
+
 @pytest.mark.parametrize("order", ["large_first", "small_first"])
 def test_server_large_oldest_runs_alone_equal_results(order):
     """The oldest resident request runs alone when it has at least 2^17 rows;
