@@ -228,7 +228,8 @@ fw_status fw_seg_profile(fw_seg *h, int32_t iters, double *ms_row_pass, double *
 fw_status fw_seg_get_stats(fw_seg *h, fw_seg_stats *stats);
 
 /* The kernel forms create chose for the handle (host data only, no device
- * call): they change no result, only the speed. */
+ * call): they change no result, only the speed.  FW_ERR_INVALID_ARG when h or
+ * forms is NULL. */
 typedef struct fw_seg_forms {
     int32_t lanes_per_row;   /* lanes per CSR row of the sparse passes */
     int32_t index_width;     /* 16: columns stored as offsets j - i; 32: as indices */
@@ -248,17 +249,20 @@ fw_status fw_seg_get_forms(fw_seg *h, fw_seg_forms *forms);
 void fw_seg_destroy(fw_seg *h);
 
 /* ------------------------------------------------------------------------
- * Batched solves: many independent problems in one persistent launch.
+ * Batched solves: many independent problems iterated together.
  *
  * All problems of a batch live in one contiguous device pool (each at its own
- * offsets) and iterate together in a cooperative persistent kernel: phase A
- * (pass A row tiles of every live problem), grid barrier, phase B, grid
- * barrier, per iteration.  Each problem keeps its own tile partition and
- * reduction order, so its iterates are bitwise the same as when it is solved
- * alone (by fw_seg_* or in any other batch).  Each problem stops on its own
- * stop rule; later launches skip it.  Waits at the grid barrier are bounded
- * by spin_budget_ms: a wait that runs out ends the launch with FW_ERR_TIMEOUT
- * instead of hanging.
+ * offsets) and iterate together, from a captured CUDA graph, in one of two
+ * schedules (FW_SCHED_*): per-item launches, where each iteration is one
+ * launch of pass A over the row tiles of every live problem and one of pass B
+ * (the kernel boundaries are the barriers); or a cooperative persistent
+ * kernel: phase A, grid barrier, phase B, grid barrier, per iteration.  Each
+ * problem keeps its own tile partition and reduction order, so its iterates
+ * are bitwise the same as when it is solved alone (by fw_seg_* or in any
+ * other batch) with the same lanes per row.  Each problem stops on its own
+ * stop rule; later launches skip it.  Waits at the persistent kernel's grid
+ * barrier are bounded by spin_budget_ms: a wait that runs out ends the launch
+ * with FW_ERR_TIMEOUT instead of hanging.
  * ---------------------------------------------------------------------- */
 
 /* A graph on the host (see fw_seg_create for the CSR conventions). */
