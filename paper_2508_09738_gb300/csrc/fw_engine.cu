@@ -936,6 +936,8 @@ fw_status fw_batch_create(fw_batch** out, int32_t P, const fw_graph* graphs,
             if (bopts->iters_per_launch < -1) return invalid("iters_per_launch must be >= -1");
             if (bopts->use_graph < FW_GRAPH_OFF || bopts->use_graph > FW_GRAPH_PREFERRED)
                 return invalid("bad use_graph");
+            if (bopts->schedule < FW_SCHED_AUTO || bopts->schedule > FW_SCHED_ITEMS)
+                return invalid("bad schedule");
         }
         std::unique_ptr<fw_batch> b(new fw_batch());
         if (bopts) b->bo = *bopts;

@@ -93,6 +93,18 @@ def test_invalid_arguments_rejected_before_device_use(libpath):
     assert e.value.status == Bd.FW_ERR_GRAPH
     with pytest.raises(Bd.FwError) as e:
         Bd.fw_seg_create(2, rp, col, w, 3, np.array([0, -1], np.int32),
+                         Bd.fw_seg_default_opts(class_table=7))
+    assert e.value.status == Bd.FW_ERR_INVALID_ARG
+    import ctypes
+    f = Bd.fw_seg_forms()
+    assert Bd.lib().fw_seg_get_forms(None, ctypes.byref(f)) == Bd.FW_ERR_INVALID_ARG
+    graphs = [type("G", (), dict(n=2, row_ptr=rp, col=col, w=w, K=3,
+                                 labels=np.array([0, -1], np.int32)))()]
+    with pytest.raises(Bd.FwError) as e:
+        Bd.fw_batch_create(graphs, Bd.fw_seg_default_opts(), Bd.fw_batch_default_opts(schedule=9))
+    assert e.value.status == Bd.FW_ERR_INVALID_ARG
+    with pytest.raises(Bd.FwError) as e:
+        Bd.fw_seg_create(2, rp, col, w, 3, np.array([0, -1], np.int32),
                          Bd.fw_seg_default_opts(eps=-1.0))
     assert e.value.status == Bd.FW_ERR_INVALID_ARG
     with pytest.raises(Bd.FwError) as e:
