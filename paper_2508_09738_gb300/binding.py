@@ -490,7 +490,8 @@ def fw_batch_destroy(b: BatchHandle) -> None:
 
 
 class Batch:
-    """Context-managed batch of independent problems (one persistent launch)."""
+    """Context-managed batch of independent problems, iterated together
+    (per-item launches or one persistent launch, autotuned)."""
 
     def __init__(self, graphs, opts=None, **bopts):
         if opts is None:

@@ -1,4 +1,5 @@
-"""Batched persistent kernel and serving loop vs single-problem solves (GPU)."""
+"""Batched solves (per-item launches and the persistent kernel) and the
+serving loop vs single-problem solves (GPU)."""
 import os
 import time
 
@@ -258,7 +259,7 @@ def test_server_rejects_and_reports_errors():
 
 def test_server_lone_requests_and_wait_any():
     """Requests submitted one at a time run alone on the server (the
-    single-problem kernels); a burst then runs in the persistent kernel.
+    single-problem kernels); a burst then shares batched epochs.
     wait_any reports every finished ticket once, and every result equals
     the request solved alone, bit for bit."""
     reqs = requests(seed=33)[:8]
